@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Throughput of periodic tricubic B-spline orbital evaluation on GB300.
+
+Metric: orbital VGH evaluations per second (positions x orbitals), with the
+evaluation kernel's fraction of the measured HBM bandwidth (roofline on
+algorithmic bytes).  One step = one spo_eval_vgh call over the whole batch
+(wrap and reduce, basis weights, 64-corner gather, tensor-product reduction
+and store, all in one kernel).
+
+Default workload: the NiO-64-shaped orbital set (64^3 grid, N = 384
+plane-wave orbitals, FP32 table of 403 MB) at 128 walkers x 768 electron
+positions (P = 98,304) - the table and the 1.51 GB of outputs per step are
+larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own positions against its own
+replica of the table (weak scaling, no data-path collective); only the timing
+uses a barrier and a max-over-ranks reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1708_02645_gb300 import inputs  # noqa: E402
+
+STORAGE_BYTES = {"f32": 4, "bf16": 2, "f16": 2}
+ROWS = {"v": 1, "vgl": 5, "vgh": 10}
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCE = os.path.join(ROOT, "paper_1708_02645_gb300", "csrc", "spo_eval.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+# ---------------------------------------------------------------------------
+# accounting
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(P: int, N: int, storage: str, kind: str) -> int:
+    """Bytes one evaluation of P positions must move at minimum per its
+    definition with no cache reuse: 64 corner coefficients and the output
+    rows per (position, orbital), plus 12 bytes of position per position."""
+    return P * N * (64 * STORAGE_BYTES[storage] + 4 * ROWS[kind]) + 12 * P
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_digest() -> str:
+    with open(KERNEL_SOURCE, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(workload: str, storage: str, kind: str):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    kernel source changed since the counters were taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    if rec.get("kernel_source_sha256_16") != kernel_source_digest():
+        return None
+    for e in rec.get("entries", []):
+        if e.get("workload") == workload and e.get("storage") == storage and e.get("kind") == kind:
+            return e.get("dram_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (timing only; the data path has no collective)
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend, init_method="env://")
+    return dist
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Each rank draws its own electron positions (weak scaling)."""
+    return base + 7919 * rank
+
+
+# ---------------------------------------------------------------------------
+# GPU clocks during the timed region (NVML through ctypes, read only)
+# ---------------------------------------------------------------------------
+REASONS = [(0x4, "sw_power_cap"), (0x8, "hw_slowdown"), (0x20, "sw_thermal_slowdown"),
+           (0x40, "hw_thermal_slowdown"), (0x80, "hw_power_brake_slowdown"),
+           (0x2, "applications_clocks_setting"), (0x10, "sync_boost")]
+
+
+def pci_bus_string(props):
+    """NVML bus id ("dddddddd:bb:dd.0") of a CUDA device, or None."""
+    try:
+        return "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    def __init__(self, pci_bus_id: str | None, period_s: float = 0.005):
+        self.samples = []
+        self.max_mhz = None
+        self.period = period_s
+        self._stop = threading.Event()
+        self._thread = None
+        self.error = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                raise RuntimeError("nvmlInit failed")
+            h = ctypes.c_void_p()
+            if pci_bus_id is None or nv.nvmlDeviceGetHandleByPciBusId_v2(
+                    pci_bus_id.encode(), ctypes.byref(h)) != 0:
+                if nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                    raise RuntimeError("no NVML device handle")
+            self.nv, self.h = nv, h
+            m = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(m)) == 0:
+                self.max_mhz = int(m.value)
+            self._reasons_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        except Exception as e:  # no NVML: report clocks as unavailable
+            self.nv = None
+            self.error = str(e)
+
+    def _sample(self):
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        p = ctypes.c_uint()
+        ok = self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0
+        self._reasons_fn(self.h, ctypes.byref(r))
+        self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(p))
+        if ok:
+            self.samples.append((int(c.value), int(r.value), int(p.value) / 1000.0))
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._sample()
+            time.sleep(self.period)
+
+    def start(self):
+        if self.nv is None:
+            return
+        self._thread = threading.Thread(target=self._run, daemon=True)
+        self._thread.start()
+
+    def stop(self):
+        if self.nv is None:
+            return
+        self._stop.set()
+        self._thread.join()
+        self._sample()
+
+    def summary(self):
+        if self.nv is None or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [],
+                    "note": f"clocks unavailable: {self.error}"}
+        mhz = [s[0] for s in self.samples]
+        bits = 0
+        for s in self.samples:
+            bits |= s[1]
+        return {"sm_mhz": float(statistics.median(mhz)), "sm_max_mhz": self.max_mhz,
+                "reasons": [name for b, name in REASONS if bits & b],
+                "samples": len(self.samples),
+                "power_w_max": max(s[2] for s in self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores, bounded sample
+# ---------------------------------------------------------------------------
+def oracle_throughput(coefs64, pos, kind: str, target_s: float, max_positions: int = 1 << 16):
+    """Time the oracle (as it stands) on a sample of the workload's positions
+    sized for about target_s seconds; returns (evals/s, positions, cores, s)."""
+    import oracle
+    k = {"v": oracle.KIND_V, "vgl": oracle.KIND_VGL, "vgh": oracle.KIND_VGH}[kind]
+    N = coefs64.shape[3]
+    n = 64
+    t0 = time.perf_counter()
+    oracle.spo_eval(coefs64, pos[:n].astype(np.float64), k)
+    dt = time.perf_counter() - t0
+    n = int(min(max_positions, len(pos), max(64, n * target_s / max(dt, 1e-6))))
+    sample = pos[:n].astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.spo_eval(coefs64, sample, k)
+    dt = time.perf_counter() - t0
+    return n * N / dt, n, oracle.num_threads(), dt
+
+
+# ---------------------------------------------------------------------------
+# arms
+# ---------------------------------------------------------------------------
+def workload_config(name: str):
+    cfg = inputs.CONFIGS[name]
+    return cfg
+
+
+def base_config(cfg, storage, kind, P):
+    return {"workload": cfg.name, "grid": list(cfg.grid), "orbitals": cfg.N, "positions": P,
+            "walkers": cfg.walkers, "electrons_per_walker": cfg.per_walker,
+            "storage": storage, "kind": kind, "coefficients": "plane waves (8 per orbital, |k|<=4)",
+            "l2": "inputs larger than L2 (table %.0f MB, outputs %.0f MB per step)" % (
+                cfg.grid[0] * cfg.grid[1] * cfg.grid[2] * ((cfg.N + 7) // 8 * 8)
+                * STORAGE_BYTES[storage] / 1e6, P * cfg.N * ROWS[kind] * 4 / 1e6)}
+
+
+def run_ours(args):
+    import torch
+    from paper_1708_02645_gb300 import spo
+
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist_init("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cfg = workload_config(args.workload)
+    kind, storage = args.kind, args.storage
+    coefs32 = cfg.make_coefs(np.float32)
+    P = cfg.P
+    pos_np = inputs.uniform_positions(P, shard_seed(cfg.seed + 1000, rank))
+    pos = torch.from_numpy(pos_np).to(dev)
+    rows = ROWS[kind]
+    out = torch.empty((P, rows, cfg.N) if rows > 1 else (P, cfg.N), dtype=torch.float32, device=dev)
+    s = spo.OrbitalSet(coefs32, storage=storage)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        s.eval(pos, kind, out=out)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler = ClockSampler(pci_bus_string(torch.cuda.get_device_properties(dev)))
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        s.eval(pos, kind, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world, dev)
+    ms_per_step = ms_max / args.steps
+    evals_per_step = P * cfg.N
+    value = world * evals_per_step / (ms_per_step * 1e-3)
+
+    # roofline of the evaluation kernel (one launch per step)
+    launch_s = (ms / args.steps) * 1e-3
+    alg = algorithmic_bytes(P, cfg.N, storage, kind)
+    achieved = alg / launch_s / 1e9
+    peak, peak_src = measured_hbm_peak()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": peak_src + " (hbm_gbs, burst copy)",
+                "traffic": recorded_traffic(cfg.name, storage, kind),
+                "algorithmic_bytes_per_launch": alg,
+                "kernel": "spo_eval_kernel<%s,%s>" % (storage, kind)}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    pos_h = torch.from_numpy(pos_np).pin_memory()
+    out_h = torch.empty(tuple(out.shape), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        s.eval_host(pos_h, kind, out=out_h)
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.eval_host(pos_h, kind, out=out_h)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    e2e = {"value": world * evals_per_step / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": int(pos_h.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 4),
+           "ms_per_step": round(e2e_s * 1e3, 4), "api": "spo_eval_host (pinned host buffers)"}
+
+    result = {
+        "metric": "orbital VGH evals/s (positions x orbitals)" if kind == "vgh"
+        else f"orbital {kind.upper()} evals/s (positions x orbitals)",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "bf16": "bf16 storage, f32 accumulate",
+                  "f16": "f16 storage, f32 accumulate"}[storage],
+        "data": "synthetic (seeded plane-wave orbitals, uniform positions)",
+        "config": base_config(cfg, storage, kind, P),
+        "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": sampler.summary(),
+    }
+    if world > 1:
+        result["config"]["parallelism"] = f"replicas x{world} (positions sharded per rank)"
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        coefs64 = cfg.make_coefs(np.float64)
+        v, n, cores, dt = oracle_throughput(coefs64, pos_np, kind, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                                  "sample": f"{n} of the {P} positions x {cfg.N} orbitals "
+                                            f"({kind.upper()}, FP64 oracle, {dt:.1f} s)"}
+    s.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle, as it stands, on the host cores: each step is a bounded
+    sample of the same workload; same metric and unit as our arm."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    cfg = workload_config(args.workload)
+    kind = args.kind
+    coefs64 = cfg.make_coefs(np.float64)
+    pos = inputs.uniform_positions(cfg.P, cfg.seed + 1000).astype(np.float64)
+    k = {"v": oracle.KIND_V, "vgl": oracle.KIND_VGL, "vgh": oracle.KIND_VGH}[kind]
+    # size one step for ~ 150 s / (steps + warmup) of oracle time
+    t0 = time.perf_counter()
+    oracle.spo_eval(coefs64, pos[:64], k)
+    per_pos = (time.perf_counter() - t0) / 64
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = int(max(16, min(cfg.P, budget / max(per_pos, 1e-9))))
+    for w in range(args.warmup):
+        oracle.spo_eval(coefs64, pos[:n], k)
+    times = []
+    for st in range(args.steps):
+        lo = (st * n) % max(1, cfg.P - n)
+        t0 = time.perf_counter()
+        oracle.spo_eval(coefs64, pos[lo:lo + n], k)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * n * cfg.N / total
+    cores = oracle.num_threads()
+    sample = f"{n} of the {cfg.P} positions x {cfg.N} orbitals per step ({kind.upper()}, FP64)"
+    result = {
+        "impl": "reference", "metric": "orbital VGH evals/s (positions x orbitals)" if kind == "vgh"
+        else f"orbital {kind.upper()} evals/s (positions x orbitals)",
+        "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded plane-wave orbitals, uniform positions)",
+        "config": base_config(cfg, "f32", kind, cfg.P),
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(result), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(inputs.CONFIGS), default=inputs.NIO64.name)
+    ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * spo.h — C ABI of libspo, GB300 (sm_103a) evaluation of periodic tricubic
+ * B-spline single-particle orbitals (SPOs).
+ *
+ * The operation (arXiv 1708.02645): the Slater matrix of Sec. 3, eq. (sj),
+ * has entries A(i,j) = phi_i(r_j); Alg. 1 needs, for each proposed electron
+ * position, the values phi_i(r) of all orbitals ("ratio", through the
+ * determinant lemma, eq. md_lemma) and their gradients and Laplacians
+ * ("derivatives").  Sec. 6.1 names the B-spline routines Bspline-v,
+ * Bspline-vgh and SPO-vgl; Sec. 6.2 describes their data as a
+ * "4-dimensional read-only table" shared by all threads, read at random and
+ * bound by memory bandwidth; Sec. 5.2 keeps that table and its evaluation in
+ * single precision.  The B-spline itself is cited, not printed, in Sec. 3;
+ * this library uses the uniform cubic B-spline on the periodic unit cube:
+ *
+ *   phi_n(r) = sum_{m in Z^3} c[m mod n][n] prod_d B3(r_d n_d - m_d)
+ *
+ * with basis function m centred on grid node (m_x/n_x, m_y/n_y, m_z/n_z).
+ *
+ * Conventions shared by every call:
+ *   - grid: n_x x n_y x n_z intervals on the unit cube, each n_d >= 4;
+ *   - coefficient table: C order [nx][ny][nz][N], orbital index fastest;
+ *   - positions: FP32, [P][3] (x, y, z per position), any finite value,
+ *     wrapped periodically; NaN or Inf give unspecified values for that
+ *     position but never an out-of-range access;
+ *   - outputs: FP32, one row of N orbitals per component, rows contiguous
+ *     per position (structure of arrays across orbitals):
+ *       V   : [P][N]
+ *       VGL : [P][5][N]    v, gx, gy, gz, lap
+ *       VGH : [P][10][N]   v, gx, gy, gz, hxx, hxy, hxz, hyy, hyz, hzz
+ *     Gradients and Hessians are Cartesian (d/dr, not d/du).
+ *   - arithmetic: FP32 accumulation for every storage type.
+ *
+ * Errors: every call returns a status.  Argument errors are detected on the
+ * host, before anything is launched, and return SPO_EINVAL (or
+ * SPO_EUNSUPPORTED); spo_last_error() then describes the problem.  CUDA
+ * errors map to SPO_ECUDA.  Evaluation calls are asynchronous on the given
+ * stream unless stated otherwise.  No C++ exception crosses this interface.
+ *
+ * Streams are passed as void* holding a cudaStream_t (NULL = the legacy
+ * default stream), so that this header needs no CUDA include.
+ */
+#ifndef SPO_H
+#define SPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPO_ABI_VERSION 1
+
+typedef enum {
+    SPO_OK = 0,
+    SPO_EINVAL = 1,        /* bad argument: null pointer, bad size, wrong memory kind */
+    SPO_ENOMEM = 2,        /* device or host allocation failed */
+    SPO_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    SPO_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    SPO_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} spo_status;
+
+typedef enum {
+    SPO_F64 = 0,   /* source coefficients only; never a storage type */
+    SPO_F32 = 1,
+    SPO_BF16 = 2,
+    SPO_F16 = 3
+} spo_dtype;
+
+typedef enum {
+    SPO_KIND_V = 0,     /* values only (Bspline-v)               1 row  */
+    SPO_KIND_VGL = 1,   /* value, gradient, Laplacian (SPO-vgl)  5 rows */
+    SPO_KIND_VGH = 2    /* value, gradient, Hessian (Bspline-vgh) 10 rows */
+} spo_kind;
+
+typedef struct {
+    int32_t nx, ny, nz;
+} spo_grid;
+
+/* Opaque orbital set: one converted coefficient table resident on one GPU. */
+typedef struct spo_set spo_set;
+
+/*
+ * spo_create — upload one orbital set (Sec. 6.2: the read-only table).
+ *
+ *   grid            n_x, n_y, n_z >= 4; the product must fit in int32.
+ *   coefs           [nx][ny][nz][N] coefficients of type src_dtype, on the
+ *                   host (coefs_on_device == 0, pageable or pinned) or on the
+ *                   current device (coefs_on_device != 0).  Read only; the
+ *                   caller keeps ownership and may free it after return.
+ *   src_dtype       SPO_F64, SPO_F32, SPO_BF16 or SPO_F16.
+ *   N               number of orbitals, >= 1.
+ *   storage         SPO_F32, SPO_BF16 or SPO_F16: type of the device table.
+ *                   Conversion rounds to nearest even, once, from src_dtype;
+ *                   FP16 subnormals are kept.
+ *   out             receives the new set.
+ *
+ * The table is stored orbital-contiguous as [nx][ny][nz][Np] on the device
+ * that is current at the call, with Np = N rounded up to a multiple of 8 and
+ * the padding orbitals set to zero.  The call is synchronous: on return the
+ * table is ready and every temporary buffer is freed.  The library owns the
+ * table until spo_destroy.
+ */
+spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dtype,
+                      int64_t N, spo_dtype storage, int coefs_on_device, spo_set **out);
+
+/* Free the set's device memory (synchronises the device first so that no
+ * queued evaluation still reads it).  NULL is accepted and ignored. */
+spo_status spo_destroy(spo_set *set);
+
+/*
+ * spo_eval_v / spo_eval_vgl / spo_eval_vgh — evaluate all N orbitals of the
+ * set at P positions (Alg. 1 "ratio" needs V; "derivatives" need VGL; the
+ * Hessian form is Bspline-vgh of Sec. 6.1).
+ *
+ *   pos     device pointer, FP32 [P][3].
+ *   P       number of positions, >= 0 (0 launches nothing).
+ *   out     device pointer, FP32, [P][N], [P][5][N] or [P][10][N].
+ *   stream  cudaStream_t to launch on.
+ *
+ * pos and out must be device (or managed) memory of the set's device, must
+ * not overlap, and must stay alive until the stream work completes.  The
+ * call returns once the kernel is queued.
+ */
+spo_status spo_eval_v(const spo_set *set, const float *pos, int64_t P, float *out, void *stream);
+spo_status spo_eval_vgl(const spo_set *set, const float *pos, int64_t P, float *out, void *stream);
+spo_status spo_eval_vgh(const spo_set *set, const float *pos, int64_t P, float *out, void *stream);
+
+/* The same three evaluations selected by kind. */
+spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                    float *out, void *stream);
+
+/*
+ * spo_eval_host — the same evaluation with HOST buffers: pos_host [P][3] and
+ * out_host ([P][rows][N]) in host memory (pinned memory gives full copy
+ * speed; pageable memory works but copies synchronously).  The positions are
+ * copied to the device, evaluated and copied back in chunks on two internal
+ * streams, so that copies overlap the kernels; the work is ordered after the
+ * work already queued on `stream`.  Synchronous: out_host is complete on
+ * return.  Device staging buffers are owned by the set, allocated on first
+ * use and reused; they are freed by spo_destroy.  Calls on the same set must
+ * not run concurrently from several host threads.
+ */
+spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
+                         float *out_host, void *stream);
+
+/* Device bytes held by the set (the converted table; staging buffers of
+ * spo_eval_host excluded). */
+spo_status spo_footprint(const spo_set *set, size_t *bytes);
+
+/* Shape of a set: grid, N, padded orbital stride Np and storage type.  Any
+ * output pointer may be NULL. */
+spo_status spo_info(const spo_set *set, spo_grid *grid, int64_t *N, int64_t *Np,
+                    spo_dtype *storage);
+
+/* Number of output rows per position for a kind (1, 5 or 10; 0 if invalid). */
+int spo_rows(spo_kind kind);
+
+/* Static description of a status code. */
+const char *spo_status_str(spo_status status);
+
+/* Description of the last error raised on the calling host thread ("" if
+ * none).  The string stays valid until the next call on this thread. */
+const char *spo_last_error(void);
+
+/* SPO_ABI_VERSION of the loaded library. */
+int spo_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPO_H */

@@ -57,6 +57,10 @@ def _bind(path: str):
         ctypes.c_void_p, ctypes.c_int]
     lib.oracle_num_threads.restype = ctypes.c_int
     lib.oracle_num_threads.argtypes = []
+    lib.oracle_spo_condition.restype = ctypes.c_int
+    lib.oracle_spo_condition.argtypes = [
+        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long,
+        ctypes.c_void_p, ctypes.c_long, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     return lib
 
 
@@ -105,3 +109,26 @@ def spo_eval(coefs: np.ndarray, pos: np.ndarray, kind: int = KIND_VGH,
     if rc != 0:
         raise ValueError(f"oracle_spo_eval failed with code {rc}")
     return out[:, 0, :] if kind == KIND_V else out
+
+
+def condition(coefs: np.ndarray, pos: np.ndarray, kind: int = KIND_VGH,
+              nthreads: int = 0) -> np.ndarray:
+    """Condition sums beta = sum |W| |c| over the window, shaped like the
+    output of spo_eval for `kind`.  For the Laplacian, beta is the sum of the
+    three diagonal Hessian betas.  A correctly implemented FP32 evaluation of
+    the same sums errs by at most a small multiple of 2^-24 * beta."""
+    lib = _load()
+    c = np.ascontiguousarray(coefs, dtype=np.float64)
+    nx, ny, nz, N = c.shape
+    r = np.ascontiguousarray(np.asarray(pos).reshape(-1, 3), dtype=np.float64)
+    P = r.shape[0]
+    b = np.empty((P, 10, N), dtype=np.float64)
+    rc = lib.oracle_spo_condition(nx, ny, nz, N, c.ctypes.data, P, r.ctypes.data,
+                                  b.ctypes.data, int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_spo_condition failed with code {rc}")
+    if kind == KIND_VGH:
+        return b
+    if kind == KIND_V:
+        return b[:, 0, :]
+    return np.concatenate([b[:, :4], (b[:, 4] + b[:, 7] + b[:, 9])[:, None]], axis=1)

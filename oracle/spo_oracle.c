@@ -230,6 +230,64 @@ int oracle_spo_eval(int nx, int ny, int nz, long N, const double *coefs,
     return failed ? -2 : 0;
 }
 
+/* Condition sums beta_q = sum over the window of |W_q| |c| for the ten VGH
+ * components, [P][10][N].  They scale the rounding-error bound of any
+ * evaluation of the same sums (a sum of 64 products computed in precision u
+ * errs by at most about 64 u beta_q).  Same window and weights as above. */
+int oracle_spo_condition(int nx, int ny, int nz, long N, const double *coefs,
+                         long P, const double *pos, double *out, int nthreads)
+{
+    if (nx < 4 || ny < 4 || nz < 4 || N < 0 || P < 0) return -1;
+    if (P == 0 || N == 0) return 0;
+    if (!coefs || !pos || !out) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (long p = 0; p < P; ++p) {
+        long ix, iy, iz;
+        double tx, ty, tz;
+        reduce_coordinate(pos[3 * p + 0], nx, &ix, &tx);
+        reduce_coordinate(pos[3 * p + 1], ny, &iy, &ty);
+        reduce_coordinate(pos[3 * p + 2], nz, &iz, &tz);
+        double wx[4], dwx[4], d2wx[4];
+        double wy[4], dwy[4], d2wy[4];
+        double wz[4], dwz[4], d2wz[4];
+        basis_weights(tx, nx, wx, dwx, d2wx);
+        basis_weights(ty, ny, wy, dwy, d2wy);
+        basis_weights(tz, nz, wz, dwz, d2wz);
+        double *h = out + (size_t)p * 10 * N;
+        for (long k = 0; k < 10 * N; ++k) h[k] = 0.0;
+        for (int a = 0; a < 4; ++a) {
+            long xa = (ix + a - 1 + nx) % nx;
+            for (int b = 0; b < 4; ++b) {
+                long yb = (iy + b - 1 + ny) % ny;
+                for (int g = 0; g < 4; ++g) {
+                    long zg = (iz + g - 1 + nz) % nz;
+                    const double *c = coefs + (((size_t)xa * ny + yb) * nz + zg) * (size_t)N;
+                    double W[10];
+                    W[0] = wx[a] * wy[b] * wz[g];
+                    W[1] = dwx[a] * wy[b] * wz[g];
+                    W[2] = wx[a] * dwy[b] * wz[g];
+                    W[3] = wx[a] * wy[b] * dwz[g];
+                    W[4] = d2wx[a] * wy[b] * wz[g];
+                    W[5] = dwx[a] * dwy[b] * wz[g];
+                    W[6] = dwx[a] * wy[b] * dwz[g];
+                    W[7] = wx[a] * d2wy[b] * wz[g];
+                    W[8] = wx[a] * dwy[b] * dwz[g];
+                    W[9] = wx[a] * wy[b] * d2wz[g];
+                    for (int q = 0; q < 10; ++q) {
+                        double *hq = h + (size_t)q * N;
+                        double aw = fabs(W[q]);
+                        for (long j = 0; j < N; ++j) hq[j] += aw * fabs(c[j]);
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
 /* number of OpenMP threads a parallel region of this library would use */
 int oracle_num_threads(void)
 {

@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libspo (include/spo.h).
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  If
+libspo.so has not been built, loading raises SpoError; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, BF16, F16 = 0, 1, 2, 3
+DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
+KIND_V, KIND_VGL, KIND_VGH = 0, 1, 2
+KINDS = {"v": KIND_V, "vgl": KIND_VGL, "vgh": KIND_VGH}
+ROWS = {KIND_V: 1, KIND_VGL: 5, KIND_VGH: 10}
+STATUS = {0: "SPO_OK", 1: "SPO_EINVAL", 2: "SPO_ENOMEM", 3: "SPO_ECUDA", 4: "SPO_ETIMEOUT",
+          5: "SPO_EUNSUPPORTED"}
+
+# every symbol include/spo.h declares: (name, restype, argtypes)
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+SIGNATURES = [
+    ("spo_create", _INT, [_P, _P, _INT, _I64, _INT, _INT, ctypes.POINTER(_P)]),
+    ("spo_destroy", _INT, [_P]),
+    ("spo_eval_v", _INT, [_P, _P, _I64, _P, _P]),
+    ("spo_eval_vgl", _INT, [_P, _P, _I64, _P, _P]),
+    ("spo_eval_vgh", _INT, [_P, _P, _I64, _P, _P]),
+    ("spo_eval", _INT, [_P, _INT, _P, _I64, _P, _P]),
+    ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
+    ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
+    ("spo_rows", _INT, [_INT]),
+    ("spo_status_str", ctypes.c_char_p, [_INT]),
+    ("spo_last_error", ctypes.c_char_p, []),
+    ("spo_abi_version", _INT, []),
+]
+
+
+class SpoError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libspo.so (raises SpoError-like RuntimeError if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    f"libspo.so is not built ({path}); build it with "
+                    "paper_1708_02645_gb300.build.build() — there is no CPU fallback")
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        detail = load().spo_last_error().decode(errors="replace")
+        raise SpoError(status, where, detail)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dtype_of(coefs, src_dtype):
+    if src_dtype is not None:
+        return DTYPES[src_dtype] if isinstance(src_dtype, str) else int(src_dtype)
+    torch = _torch()
+    if isinstance(coefs, torch.Tensor):
+        m = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16, torch.float16: F16}
+        if coefs.dtype not in m:
+            raise TypeError(f"unsupported coefficient dtype {coefs.dtype}")
+        return m[coefs.dtype]
+    m = {np.dtype(np.float64): F64, np.dtype(np.float32): F32, np.dtype(np.float16): F16}
+    if coefs.dtype not in m:
+        raise TypeError(f"unsupported coefficient dtype {coefs.dtype} (pass src_dtype for raw bf16)")
+    return m[coefs.dtype]
+
+
+class OrbitalSet:
+    """One B-spline orbital set resident on the current CUDA device.
+
+    coefs: [nx, ny, nz, N] coefficients, numpy (host) or torch (host or
+    device), FP64/FP32/FP16, torch BF16, or a raw uint16 numpy array with
+    src_dtype="bf16".  storage: "f32", "bf16" or "f16".
+    """
+
+    def __init__(self, coefs, storage: str = "f32", src_dtype=None):
+        lib = load()
+        torch = _torch()
+        sd = _dtype_of(coefs, src_dtype)
+        on_device = isinstance(coefs, torch.Tensor) and coefs.is_cuda
+        if isinstance(coefs, torch.Tensor):
+            coefs = coefs.contiguous()
+            keep = coefs
+            ptr = coefs.data_ptr()
+        else:
+            keep = np.ascontiguousarray(coefs)
+            ptr = keep.ctypes.data
+        if len(keep.shape) != 4:
+            raise ValueError("coefs must be [nx, ny, nz, N]")
+        nx, ny, nz, N = (int(s) for s in keep.shape)
+        grid = _Grid(nx, ny, nz)
+        h = ctypes.c_void_p()
+        _check(lib.spo_create(ctypes.byref(grid), ctypes.c_void_p(ptr), sd, N, DTYPES[storage],
+                              int(on_device), ctypes.byref(h)), "spo_create")
+        self._h = h
+        self.grid = (nx, ny, nz)
+        self.N = N
+        self.storage = storage
+        self.device = torch.cuda.current_device()
+        del keep
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("orbital set already destroyed")
+        return self._h
+
+    def footprint(self) -> int:
+        b = ctypes.c_size_t()
+        _check(load().spo_footprint(self.handle, ctypes.byref(b)), "spo_footprint")
+        return int(b.value)
+
+    def info(self):
+        g = _Grid()
+        n, npad, st = _I64(), _I64(), _INT()
+        _check(load().spo_info(self.handle, ctypes.byref(g), ctypes.byref(n), ctypes.byref(npad),
+                               ctypes.byref(st)), "spo_info")
+        return {"grid": (g.nx, g.ny, g.nz), "N": n.value, "Np": npad.value, "storage": st.value}
+
+    def out_shape(self, P: int, kind) -> tuple:
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        return (P, self.N) if k == KIND_V else (P, ROWS[k], self.N)
+
+    def eval(self, pos, kind="vgh", out=None, stream=None):
+        """Evaluate at device positions pos [P, 3] (FP32 torch CUDA tensor).
+        Returns out (allocated if None): [P, N], [P, 5, N] or [P, 10, N]."""
+        torch = _torch()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dtype == torch.float32):
+            raise TypeError("pos must be a float32 CUDA tensor")
+        if pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+            raise ValueError("pos must be a contiguous [P, 3] tensor")
+        P = int(pos.shape[0])
+        if out is None:
+            out = torch.empty(self.out_shape(P, k), dtype=torch.float32, device=pos.device)
+        elif not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+                  and out.numel() == P * ROWS[k] * self.N):
+            raise ValueError("out must be a contiguous float32 CUDA tensor of the output shape")
+        _check(load().spo_eval(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
+                               ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "spo_eval")
+        return out
+
+    def eval_v(self, pos, out=None, stream=None):
+        return self.eval(pos, "v", out, stream)
+
+    def eval_vgl(self, pos, out=None, stream=None):
+        return self.eval(pos, "vgl", out, stream)
+
+    def eval_vgh(self, pos, out=None, stream=None):
+        return self.eval(pos, "vgh", out, stream)
+
+    def eval_host(self, pos, kind="vgh", out=None, stream=None):
+        """Evaluate host positions (numpy or CPU tensor, FP32 [P, 3]) into a
+        host output (numpy/CPU tensor, allocated if None).  Synchronous."""
+        torch = _torch()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        if isinstance(pos, torch.Tensor):
+            if pos.is_cuda or pos.dtype != torch.float32 or not pos.is_contiguous():
+                raise TypeError("pos must be a contiguous float32 CPU tensor")
+            pptr, P = pos.data_ptr(), int(pos.shape[0])
+        else:
+            pos = np.ascontiguousarray(pos, dtype=np.float32)
+            pptr, P = pos.ctypes.data, int(pos.shape[0])
+        if out is None:
+            out = np.empty(self.out_shape(P, k), dtype=np.float32)
+        if isinstance(out, torch.Tensor):
+            if out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous() \
+                    or out.numel() != P * ROWS[k] * self.N:
+                raise ValueError("out must be a contiguous float32 CPU tensor of the output shape")
+            optr = out.data_ptr()
+        else:
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size != P * ROWS[k] * self.N:
+                raise ValueError("out must be a contiguous float32 array of the output shape")
+            optr = out.ctypes.data
+        _check(load().spo_eval_host(self.handle, k, ctypes.c_void_p(pptr), P, ctypes.c_void_p(optr),
+                                    _stream_handle(stream)), "spo_eval_host")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().spo_destroy(self._h), "spo_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,290 @@
+"""GPU (libspo, sm_103a) vs FP64 oracle, element by element, through the C ABI.
+
+Inputs come from the seeded recipes in paper_1708_02645_gb300.inputs; every
+expected value comes from the oracle.  Kernel parity runs the oracle on the
+coefficients exactly as the table stores them; the storage-format error runs
+it on the original FP64 coefficients.  Tolerances are in tests/parity.py.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_02645_gb300 import inputs
+from parity import (assert_format_error, assert_kernel_parity, errors, stored_values)
+
+pytestmark = pytest.mark.gpu
+
+KINDS = {"v": 0, "vgl": 1, "vgh": 2}
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None):
+    t = torch()
+    with spo.OrbitalSet(coefs_upload, storage=storage, src_dtype=src_dtype) as s:
+        p = t.from_numpy(np.ascontiguousarray(pos, dtype=np.float32)).cuda()
+        o = s.eval(p, kind, out=out)
+        t.cuda.synchronize()
+        return o.cpu().numpy()
+
+
+def check_case(spo, coefs64, pos, kind, storage, sample=None, what=""):
+    """Kernel parity (and the format error for reduced precision)."""
+    k = KINDS[kind]
+    vals, upload, sd = stored_values(coefs64, storage)
+    got = gpu_eval(spo, upload, pos, kind, storage, sd)
+    idx = np.arange(len(pos)) if sample is None else sample
+    pos64 = np.asarray(pos, dtype=np.float64)[idx]
+    ref = oracle.spo_eval(vals, pos64, k)
+    beta = oracle.condition(vals, pos64, k)
+    err = assert_kernel_parity(got[idx], ref, beta, k, what)
+    if storage != "f32":
+        ref64 = oracle.spo_eval(coefs64, pos64, k)
+        beta64 = oracle.condition(coefs64, pos64, k)
+        wsum = oracle.condition(np.ones(coefs64.shape[:3] + (1,)), pos64, k)
+        wsum = np.broadcast_to(wsum, ref64.shape)
+        assert_format_error(got[idx], ref64, beta64, wsum, k, storage, what)
+    return err
+
+
+# ---------------------------------------------------------------------------
+# the workloads
+# ---------------------------------------------------------------------------
+def test_uniform16_vgh(spo_lib, oracle_lib):
+    cfg = inputs.UNIFORM16
+    c = cfg.make_coefs()
+    check_case(spo_lib, c, cfg.make_positions(), "vgh", "f32", what=cfg.name)
+
+
+@pytest.mark.parametrize("kind", ["vgl", "vgh", "v"])
+def test_nio32_full(spo_lib, oracle_lib, kind):
+    cfg = inputs.NIO32
+    c = cfg.make_coefs()
+    check_case(spo_lib, c, cfg.make_positions(), kind, "f32", what=f"{cfg.name} {kind}")
+
+
+@pytest.fixture(scope="module")
+def nio64():
+    cfg = inputs.NIO64
+    return cfg, cfg.make_coefs(), cfg.make_positions()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_nio64_full_batch_sampled(spo_lib, oracle_lib, nio64, storage):
+    """All 98,304 positions in one launch (the benchmark's launch); the oracle
+    checks a seeded sample of 2048 of them element by element."""
+    cfg, c, pos = nio64
+    sample = np.sort(np.unique((inputs.uniform01(99, 2048) * len(pos)).astype(np.int64)))
+    check_case(spo_lib, c, pos, "vgh", storage, sample=sample, what=f"{cfg.name} {storage}")
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("grid,N", [((4, 4, 4), 1), ((5, 9, 7), 13), ((4, 6, 5), 7),
+                                    ((8, 8, 8), 33), ((7, 4, 11), 4), ((6, 6, 6), 1024)])
+@pytest.mark.parametrize("kind", ["v", "vgl", "vgh"])
+def test_ragged_shapes(spo_lib, oracle_lib, grid, N, kind):
+    c = inputs.uniform_coefs(*grid, N, seed=grid[0] * 100 + N)
+    pos = np.concatenate([inputs.uniform_positions(301, 5), inputs.wide_positions(200, 6)])
+    check_case(spo_lib, c, pos, kind, "f32", what=f"{grid} N={N} {kind}")
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_ragged_reduced_precision(spo_lib, oracle_lib, storage):
+    c = inputs.plane_wave_coefs(9, 10, 11, 21, seed=3)
+    pos = inputs.wide_positions(257, 8)
+    check_case(spo_lib, c, pos, "vgh", storage, what=f"ragged {storage}")
+
+
+def test_special_positions(spo_lib, oracle_lib):
+    """Grid nodes, cell faces, 1.0, negative and large coordinates."""
+    grid = (8, 12, 10)
+    c = inputs.uniform_coefs(*grid, 12, seed=12)
+    g = np.array(grid, dtype=np.float64)
+    nodes = np.array([[0, 0, 0], [7, 11, 9], [3, 6, 5], [8, 12, 10]]) / g
+    pts = np.concatenate([nodes, [[1.0, 1.0, 1.0], [-1.0, -0.5, 2.0], [0.99999994, 0.0, 0.5],
+                                  [-1e-7, 1e-7, -0.99999994], [123.25, -77.5, 1000.125]],
+                          nodes - 1e-7, nodes + 1e-7]).astype(np.float32)
+    check_case(spo_lib, c, pts, "vgh", "f32", what="special positions")
+
+
+def test_nonfinite_positions_do_not_fault(spo_lib, oracle_lib):
+    """NaN/Inf give unspecified values for that position only."""
+    t = torch()
+    c = inputs.uniform_coefs(6, 6, 6, 8, seed=1)
+    pos = inputs.uniform_positions(64, 2)
+    bad = pos.copy()
+    bad[5] = [np.nan, 0.5, 0.5]
+    bad[9] = [np.inf, -np.inf, 0.25]
+    bad[17] = [3e38, -3e38, np.nan]
+    with spo_lib.OrbitalSet(c.astype(np.float32)) as s:
+        o = s.eval(t.from_numpy(bad).cuda(), "vgh")
+        t.cuda.synchronize()
+        got = o.cpu().numpy()
+    good = np.setdiff1d(np.arange(64), [5, 9, 17])
+    vals = c.astype(np.float32).astype(np.float64)
+    ref = oracle.spo_eval(vals, pos[good].astype(np.float64), 2)
+    beta = oracle.condition(vals, pos[good].astype(np.float64), 2)
+    assert_kernel_parity(got[good], ref, beta, 2, "finite neighbours of NaN positions")
+
+
+def test_empty_batch(spo_lib):
+    t = torch()
+    c = inputs.uniform_coefs(4, 4, 4, 3, seed=1).astype(np.float32)
+    with spo_lib.OrbitalSet(c) as s:
+        o = s.eval(t.empty((0, 3), device="cuda"), "vgh")
+        assert o.shape == (0, 10, 3)
+        h = s.eval_host(np.empty((0, 3), np.float32), "vgl")
+        assert h.shape == (0, 5, 3)
+
+
+def test_misaligned_output_uses_scalar_stores(spo_lib, oracle_lib):
+    t = torch()
+    c = inputs.uniform_coefs(5, 6, 7, 16, seed=4)
+    pos = inputs.uniform_positions(100, 3)
+    with spo_lib.OrbitalSet(c.astype(np.float32)) as s:
+        big = t.full((100 * 10 * 16 + 1,), float("nan"), device="cuda")
+        view = big[1:]   # 4-byte aligned, not 16-byte aligned
+        s.eval(t.from_numpy(pos).cuda(), "vgh", out=view)
+        t.cuda.synchronize()
+        got = view.cpu().numpy().reshape(100, 10, 16)
+        assert np.isnan(big[0].item())
+    vals = c.astype(np.float32).astype(np.float64)
+    ref = oracle.spo_eval(vals, pos, 2)
+    assert_kernel_parity(got, ref, oracle.condition(vals, pos, 2), 2, "misaligned out")
+
+
+def test_table_beyond_2_31_elements(spo_lib):
+    """A 128^3 x 1024 FP32 table (2^31 coefficients, 8.6 GB): element offsets
+    beyond int32.  Coefficients c[m][j] = (j mod 5) + m_x + 2 m_y + 3 m_z are
+    linear in m, so by polynomial reproduction (pinned in the oracle tests)
+    V = (j mod 5) + u_x + 2 u_y + 3 u_z, G = (n_x, 2 n_y, 3 n_z), H = 0 in
+    cells whose window does not wrap.  Addressing errors would break this."""
+    t = torch()
+    n, N = 128, 1024
+    ar = t.arange(n, device="cuda", dtype=t.float32)
+    coefs = (ar[:, None, None, None] + 2 * ar[None, :, None, None] + 3 * ar[None, None, :, None]
+             + (t.arange(N, device="cuda") % 5).float()[None, None, None, :])
+    P = 2048
+    u = 0.999 * inputs.uniform01(81, 3 * P).reshape(P, 3)   # stay inside the cell
+    cells = 1 + np.floor(inputs.uniform01(82, 3 * P).reshape(P, 3) * (n - 3))
+    pos = ((cells + u) / n).astype(np.float32)
+    with spo_lib.OrbitalSet(coefs) as s:
+        del coefs
+        t.cuda.empty_cache()
+        got = s.eval_vgh(t.from_numpy(pos).cuda()).cpu().numpy().astype(np.float64)
+    uu = pos.astype(np.float64) * n
+    v = (np.arange(N) % 5)[None, :] + (uu[:, 0] + 2 * uu[:, 1] + 3 * uu[:, 2])[:, None]
+    assert np.abs(got[:, 0] - v).max() <= 1e-5 * np.abs(v).max()
+    for d, g in enumerate((n, 2 * n, 3 * n)):
+        assert np.abs(got[:, 1 + d] - g).max() <= 1e-5 * g
+    assert np.abs(got[:, 4:]).max() <= 1e-5 * 6 * n * n
+
+
+# ---------------------------------------------------------------------------
+# consistency between entry points
+# ---------------------------------------------------------------------------
+def test_kinds_consistent(spo_lib):
+    t = torch()
+    c = inputs.plane_wave_coefs(12, 12, 12, 40, seed=9).astype(np.float32)
+    pos = t.from_numpy(inputs.wide_positions(500, 10)).cuda()
+    with spo_lib.OrbitalSet(c) as s:
+        v, g, h = s.eval_v(pos), s.eval_vgl(pos), s.eval_vgh(pos)
+        t.cuda.synchronize()
+    v, g, h = v.cpu().numpy(), g.cpu().numpy(), h.cpu().numpy()
+    # identical z/y/x stages for the value: bitwise equal
+    assert np.array_equal(v, h[:, 0]) and np.array_equal(g[:, :4], h[:, :4])
+    lap = h[:, 4].astype(np.float64) + h[:, 7] + h[:, 9]
+    assert np.abs(g[:, 4] - lap).max() <= 1e-5 * np.abs(lap).max()
+
+
+def test_host_path_matches_device_path(spo_lib):
+    """spo_eval_host (chunked, two streams) gives the device path's bits,
+    including a ragged last chunk."""
+    t = torch()
+    c = inputs.plane_wave_coefs(8, 8, 8, 384, seed=11).astype(np.float32)
+    pos = inputs.wide_positions(10001, 12)   # > 2 chunks of 4369 VGH positions
+    with spo_lib.OrbitalSet(c) as s:
+        dev = s.eval(t.from_numpy(pos).cuda(), "vgh").cpu().numpy()
+        pinned = t.empty((10001, 10, 384), dtype=t.float32).pin_memory()
+        host = s.eval_host(t.from_numpy(pos).pin_memory(), "vgh", out=pinned).numpy()
+        pageable = s.eval_host(pos, "vgh")
+    assert np.array_equal(dev, host) and np.array_equal(dev, pageable)
+
+
+def test_deterministic(spo_lib):
+    t = torch()
+    c = inputs.plane_wave_coefs(16, 16, 16, 64, seed=13).astype(np.float32)
+    pos = t.from_numpy(inputs.uniform_positions(3000, 14)).cuda()
+    with spo_lib.OrbitalSet(c) as s:
+        a = s.eval_vgh(pos).cpu().numpy()
+        b = s.eval_vgh(pos).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# upload and conversion
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+def test_library_conversion_rounds_once_to_nearest_even(spo_lib, storage):
+    """F64 coefficients converted by the library give the same outputs, bit
+    for bit, as coefficients rounded on the host with one RNE step."""
+    t = torch()
+    c = inputs.plane_wave_coefs(8, 9, 10, 24, seed=15)
+    _, upload, sd = stored_values(c, storage)
+    pos = t.from_numpy(inputs.uniform_positions(700, 16)).cuda()
+    with spo_lib.OrbitalSet(c, storage=storage) as a, \
+            spo_lib.OrbitalSet(upload, storage=storage, src_dtype=sd) as b, \
+            spo_lib.OrbitalSet(t.from_numpy(c).cuda(), storage=storage) as d:
+        oa, ob, od = a.eval_vgh(pos), b.eval_vgh(pos), d.eval_vgh(pos)
+        t.cuda.synchronize()
+        assert t.equal(oa, ob) and t.equal(oa, od)
+        assert a.info()["Np"] == 24 and a.footprint() == 8 * 9 * 10 * 24 * (4 if storage == "f32" else 2)
+
+
+def test_footprint_and_padding(spo_lib):
+    c = inputs.uniform_coefs(4, 5, 6, 13, seed=1).astype(np.float32)
+    with spo_lib.OrbitalSet(c, storage="bf16") as s:
+        info = s.info()
+        assert info["grid"] == (4, 5, 6) and info["N"] == 13 and info["Np"] == 16
+        assert s.footprint() == 4 * 5 * 6 * 16 * 2
+
+
+def test_errors_are_reported_not_launched(spo_lib):
+    t = torch()
+    c = inputs.uniform_coefs(4, 4, 4, 4, seed=1).astype(np.float32)
+    with spo_lib.OrbitalSet(c) as s:
+        host_pos = t.zeros((4, 3))
+        out = t.empty((4, 10, 4), device="cuda")
+        import ctypes
+        lib = spo_lib.load()
+        st = lib.spo_eval(s.handle, 2, ctypes.c_void_p(host_pos.data_ptr()), 4,
+                          ctypes.c_void_p(out.data_ptr()), None)
+        assert st == 1 and b"device memory" in lib.spo_last_error()
+        st = lib.spo_eval(s.handle, 2, ctypes.c_void_p(out.data_ptr()), -1,
+                          ctypes.c_void_p(out.data_ptr()), None)
+        assert st == 1
+        st = lib.spo_eval(s.handle, 2, ctypes.c_void_p(out.data_ptr()), 1 << 40,
+                          ctypes.c_void_p(out.data_ptr()), None)
+        assert st == 1 and b"too large" in lib.spo_last_error()
+        with pytest.raises(spo_lib.SpoError):
+            spo_lib.OrbitalSet(c, storage="f64")
+        # the context is still healthy
+        o = s.eval_vgh(t.from_numpy(inputs.uniform_positions(8, 1)).cuda())
+        t.cuda.synchronize()
+        assert t.isfinite(o).all()
+
+
+def test_nio32_errors_reported(spo_lib, oracle_lib):
+    """max and RMS relative error per output group, FP32 storage (reported)."""
+    cfg = inputs.NIO32
+    c = cfg.make_coefs()
+    pos = cfg.make_positions()[:2048]
+    got = gpu_eval(spo_lib, c.astype(np.float32), pos, "vgl", "f32")
+    ref = oracle.spo_eval(c, pos.astype(np.float64), 1)
+    e = errors(got, ref, 1)
+    assert all(v["max_rel"] < 1e-5 for v in e.values()), e
