@@ -212,22 +212,26 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on the host cores, bounded sample
 # ---------------------------------------------------------------------------
-def oracle_throughput(coefs64, pos, kind: str, target_s: float, max_positions: int = 1 << 16):
+def oracle_throughput(coefs64, pos, kind: str, target_s: float):
     """Time the oracle (as it stands) on a sample of the workload's positions
-    sized for about target_s seconds; returns (evals/s, positions, cores, s)."""
+    sized for about target_s seconds of CPU work (the whole batch, repeated,
+    when one pass is shorter than that).  Returns (evals/s, positions per
+    pass, passes, cores, seconds)."""
     import oracle
     k = {"v": oracle.KIND_V, "vgl": oracle.KIND_VGL, "vgh": oracle.KIND_VGH}[kind]
     N = coefs64.shape[3]
-    n = 64
+    n0 = min(len(pos), 256)
     t0 = time.perf_counter()
-    oracle.spo_eval(coefs64, pos[:n].astype(np.float64), k)
-    dt = time.perf_counter() - t0
-    n = int(min(max_positions, len(pos), max(64, n * target_s / max(dt, 1e-6))))
+    oracle.spo_eval(coefs64, pos[:n0].astype(np.float64), k)
+    per_pos = max((time.perf_counter() - t0) / n0, 1e-9)
+    n = int(min(len(pos), max(n0, target_s / per_pos)))
+    reps = max(1, int(round(target_s / (per_pos * n))))
     sample = pos[:n].astype(np.float64)
     t0 = time.perf_counter()
-    oracle.spo_eval(coefs64, sample, k)
+    for _ in range(reps):
+        oracle.spo_eval(coefs64, sample, k)
     dt = time.perf_counter() - t0
-    return n * N / dt, n, oracle.num_threads(), dt
+    return reps * n * N / dt, n, reps, oracle.num_threads(), dt
 
 
 # ---------------------------------------------------------------------------
@@ -247,6 +251,26 @@ def base_config(cfg, storage, kind, P):
                 * STORAGE_BYTES[storage] / 1e6, P * cfg.N * ROWS[kind] * 4 / 1e6)}
 
 
+def measure_e2e(args, s, pos_np, out, kind, evals_per_step, world, dev):
+    """Same metric through spo_eval_host: pinned host positions in, pinned
+    host outputs back, both copies inside the timed region."""
+    import torch
+    pos_h = torch.from_numpy(pos_np).pin_memory()
+    out_h = torch.empty(tuple(out.shape), dtype=torch.float32).pin_memory()
+    for _ in range(max(1, min(args.warmup, 2))):
+        s.eval_host(pos_h, kind, out=out_h)
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.eval_host(pos_h, kind, out=out_h)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
+    e2e = {"value": world * evals_per_step / e2e_s, "unit": "evals/s",
+           "h2d_bytes_per_step": int(pos_h.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 4),
+           "ms_per_step": round(e2e_s * 1e3, 4), "api": "spo_eval_host (pinned host buffers)"}
+    return e2e
+
+
 def run_ours(args):
     import torch
     from paper_1708_02645_gb300 import spo
@@ -259,7 +283,7 @@ def run_ours(args):
     cfg = workload_config(args.workload)
     kind, storage = args.kind, args.storage
     coefs32 = cfg.make_coefs(np.float32)
-    P = cfg.P
+    P = args.positions if args.positions > 0 else cfg.P
     pos_np = inputs.uniform_positions(P, shard_seed(cfg.seed + 1000, rank))
     pos = torch.from_numpy(pos_np).to(dev)
     rows = ROWS[kind]
@@ -301,19 +325,7 @@ def run_ours(args):
                 "kernel": "spo_eval_kernel<%s,%s>" % (storage, kind)}
 
     # end to end through the C ABI with host buffers (pinned), copies timed
-    pos_h = torch.from_numpy(pos_np).pin_memory()
-    out_h = torch.empty(tuple(out.shape), dtype=torch.float32).pin_memory()
-    for _ in range(max(1, min(args.warmup, 2))):
-        s.eval_host(pos_h, kind, out=out_h)
-    e2e_steps = max(1, min(args.steps, 10))
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        s.eval_host(pos_h, kind, out=out_h)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
-    e2e = {"value": world * evals_per_step / e2e_s, "unit": "evals/s",
-           "h2d_bytes_per_step": int(pos_h.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 4),
-           "ms_per_step": round(e2e_s * 1e3, 4), "api": "spo_eval_host (pinned host buffers)"}
+    e2e = None if args.no_e2e else measure_e2e(args, s, pos_np, out, kind, evals_per_step, world, dev)
 
     result = {
         "metric": "orbital VGH evals/s (positions x orbitals)" if kind == "vgh"
@@ -333,10 +345,11 @@ def run_ours(args):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         coefs64 = cfg.make_coefs(np.float64)
-        v, n, cores, dt = oracle_throughput(coefs64, pos_np, kind, args.cpu_seconds)
+        v, n, reps, cores, dt = oracle_throughput(coefs64, pos_np, kind, args.cpu_seconds)
         result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                                  "sample": f"{n} of the {P} positions x {cfg.N} orbitals "
-                                            f"({kind.upper()}, FP64 oracle, {dt:.1f} s)"}
+                                  "sample": f"{n} of the {P} positions x {cfg.N} orbitals, "
+                                            f"{reps} pass(es) ({kind.upper()}, FP64 oracle, "
+                                            f"{dt:.1f} s on {cores} threads)"}
     s.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -402,6 +415,9 @@ def main(argv=None):
     ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--positions", type=int, default=0,
+                    help="evaluate this many positions instead of the workload's (profiling)")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
