@@ -1,0 +1,92 @@
+"""Host logic of bench.py: byte accounting, traffic records, and the
+multi-rank timing reduction (world size 2, gloo, CPU processes)."""
+import json
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def test_algorithmic_bytes_per_eval():
+    # 64 coefficients + output rows per (position, orbital), 12 B per position
+    assert bench.algorithmic_bytes(1, 1, "f32", "vgh") == 64 * 4 + 40 + 12
+    assert bench.algorithmic_bytes(1, 1, "bf16", "vgh") == 64 * 2 + 40 + 12
+    assert bench.algorithmic_bytes(1, 1, "f16", "vgl") == 64 * 2 + 20 + 12
+    assert bench.algorithmic_bytes(1, 1, "f32", "v") == 64 * 4 + 4 + 12
+    assert bench.algorithmic_bytes(98304, 384, "f32", "vgh") == 98304 * 384 * 296 + 12 * 98304
+
+
+def test_traffic_record_is_dropped_when_kernel_changes(tmp_path, monkeypatch):
+    rec = {"kernel_source_sha256_16": bench.kernel_source_digest(),
+           "entries": [{"workload": "w", "storage": "f32", "kind": "vgh",
+                        "dram_bytes_per_launch": 123}]}
+    path = tmp_path / "t.json"
+    path.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    assert bench.recorded_traffic("w", "f32", "vgh") == 123
+    assert bench.recorded_traffic("w", "bf16", "vgh") is None
+    rec["kernel_source_sha256_16"] = "0" * 16
+    path.write_text(json.dumps(rec))
+    assert bench.recorded_traffic("w", "f32", "vgh") is None
+
+
+def test_shard_seeds_differ_per_rank():
+    seeds = {bench.shard_seed(100, r) for r in range(8)}
+    assert len(seeds) == 8
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    r, w, _ = bench.dist_env()
+    bench.dist_init("gloo")
+    bench.barrier(w)
+    # each rank "measured" a different time; every rank must see the max
+    m = bench.max_over_ranks(10.0 + 5.0 * r, w)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+    q.put((r, m))
+
+
+def test_max_over_ranks_gloo_world2():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == {0: 15.0, 1: 15.0}
+
+
+def test_reference_arm_rank_nonzero_exits_without_work(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert capsys.readouterr().out == ""
+
+
+@pytest.mark.slow
+def test_reference_arm_prints_one_line(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    bench.main(["--impl", "reference", "--steps", "2", "--warmup", "3",
+                "--workload", "uniform16_n16"])
+    line = capsys.readouterr().out.strip()
+    d = json.loads(line)
+    assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
