@@ -78,13 +78,21 @@ typedef struct {
     int32_t nx, ny, nz;
 } spo_grid;
 
+/* Evaluation strategy (all give the same values; see spo_eval_ex). */
+typedef enum {
+    SPO_ALGO_AUTO = 0,           /* library's choice from the batch shape */
+    SPO_ALGO_GATHER = 1,         /* positions in given order, corner rows from global memory */
+    SPO_ALGO_SORTED_GATHER = 2,  /* positions binned by brick first, then gathered */
+    SPO_ALGO_BRICK = 3           /* binned; each brick's table block staged in shared memory */
+} spo_algo;
+
 /* Opaque orbital set: one converted coefficient table resident on one GPU. */
 typedef struct spo_set spo_set;
 
 /*
  * spo_create — upload one orbital set (Sec. 6.2: the read-only table).
  *
- *   grid            n_x, n_y, n_z >= 4; the product must fit in int32.
+ *   grid            n_x, n_y, n_z >= 4.
  *   coefs           [nx][ny][nz][N] coefficients of type src_dtype, on the
  *                   host (coefs_on_device == 0, pageable or pinned) or on the
  *                   current device (coefs_on_device != 0).  Read only; the
@@ -96,9 +104,11 @@ typedef struct spo_set spo_set;
  *                   FP16 subnormals are kept.
  *   out             receives the new set.
  *
- * The table is stored orbital-contiguous as [nx][ny][nz][Np] on the device
- * that is current at the call, with Np = N rounded up to a multiple of 8 and
- * the padding orbitals set to zero.  The call is synchronous: on return the
+ * The table is stored orbital-contiguous as [nx+3][ny+3][nz+3][Np] on the
+ * device that is current at the call: padded node i' holds grid node
+ * (i' - 1) mod n (3 ghost nodes per axis, so that every 4x4x4 window is a
+ * contiguous box), Np = N rounded up to a multiple of 8, padding orbitals
+ * zero.  (nx+3)(ny+3)(nz+3) must fit in int32.  The call is synchronous: on return the
  * table is ready and every temporary buffer is freed.  The library owns the
  * table until spo_destroy.
  */
@@ -127,9 +137,51 @@ spo_status spo_eval_v(const spo_set *set, const float *pos, int64_t P, float *ou
 spo_status spo_eval_vgl(const spo_set *set, const float *pos, int64_t P, float *out, void *stream);
 spo_status spo_eval_vgh(const spo_set *set, const float *pos, int64_t P, float *out, void *stream);
 
-/* The same three evaluations selected by kind. */
+/* The same three evaluations selected by kind (strategy SPO_ALGO_AUTO). */
 spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
                     float *out, void *stream);
+
+/*
+ * spo_eval_ex — spo_eval with an explicit strategy.  The binned strategies
+ * first sort the positions by brick of 4x4x4 cells (a counting sort in
+ * device scratch memory owned by the set, one scratch area per stream,
+ * allocated on first use of a stream or by spo_reserve, freed by
+ * spo_destroy); SPO_ALGO_BRICK then stages each brick's 7x7x7-node block of
+ * the table in shared memory with one TMA copy per orbital tile.  Every
+ * strategy evaluates the same sums in the same order: outputs are
+ * bit-identical across strategies.  SPO_ALGO_BRICK needs at least 64
+ * padded orbitals and returns SPO_EUNSUPPORTED otherwise; binned strategies need P < 2^31.  Calls with the same set and
+ * stream are ordered by the stream; calls on different streams use
+ * different scratch areas.  A call that allocates scratch synchronises the
+ * device and cannot be captured in a CUDA graph: call spo_reserve first.
+ */
+spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                       float *out, void *stream, spo_algo algo);
+
+/*
+ * spo_bin / spo_eval_binned — the two stages of the binned strategies, for
+ * callers that evaluate several kinds at the same positions (for example V
+ * for the ratio and then VGL for the derivatives of an accepted move, Alg. 1).
+ * spo_bin sorts pos (device, [P][3]) by brick into the scratch of `stream`;
+ * spo_eval_binned then evaluates with algo SPO_ALGO_SORTED_GATHER or
+ * SPO_ALGO_BRICK from that binning, and must receive the same pos and P as
+ * the last spo_bin on the same set and stream (else SPO_EINVAL).  pos must
+ * not change in between.
+ */
+spo_status spo_bin(const spo_set *set, const float *pos, int64_t P, void *stream);
+spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                           float *out, void *stream, spo_algo algo);
+
+/* Allocate (or grow) the set's scratch for `stream` to hold batches of up to
+ * P positions, so that later evaluations on that stream allocate nothing.
+ * Synchronous. */
+spo_status spo_reserve(spo_set *set, int64_t P, void *stream);
+
+/* Device-side status word of the current device: bit 0 = a bounded wait on a
+ * TMA copy gave up (the affected outputs are incomplete).  Synchronises
+ * `stream`; with clear != 0 the word is reset to zero afterwards.  Returns
+ * SPO_ETIMEOUT if bit 0 was set, SPO_OK otherwise. */
+spo_status spo_device_status(unsigned int *flags, int clear, void *stream);
 
 /*
  * spo_eval_host — the same evaluation with HOST buffers: pos_host [P][3] and
@@ -145,7 +197,7 @@ spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t
 spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
                          float *out_host, void *stream);
 
-/* Device bytes held by the set (the converted table; staging buffers of
+/* Device bytes held by the set's table (scratch and the staging buffers of
  * spo_eval_host excluded). */
 spo_status spo_footprint(const spo_set *set, size_t *bytes);
 

@@ -1,8 +1,10 @@
 // Host side of the libspo C ABI: argument checks, table upload and
-// conversion, launch dispatch, the host-buffer pipeline and error reporting.
+// conversion, strategy dispatch, per-stream scratch, the host-buffer
+// pipeline and error reporting.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +14,8 @@
 #include "spo_internal.h"
 
 namespace {
+
+using spo_detail::fail;
 
 thread_local char g_last_error[512] = "";
 
@@ -45,7 +49,7 @@ size_t dtype_size(spo_dtype t) {
 bool valid_kind(spo_kind k) { return k == SPO_KIND_V || k == SPO_KIND_VGL || k == SPO_KIND_VGH; }
 
 spo_status cuda_fail(cudaError_t e, const char *what) {
-    return spo_detail::fail(SPO_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return fail(SPO_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
 // pointer must be device or managed memory on `device`
@@ -53,30 +57,150 @@ spo_status check_device_pointer(const void *ptr, int device, const char *name) {
     cudaPointerAttributes attr;
     cudaError_t e = cudaPointerGetAttributes(&attr, ptr);
     if (e != cudaSuccess) {
-        cudaGetLastError();   // clear the sticky-free error of this query
-        return spo_detail::fail(SPO_EINVAL, "%s is not a CUDA pointer", name);
+        cudaGetLastError();   // clear the error of this query
+        return fail(SPO_EINVAL, "%s is not a CUDA pointer", name);
     }
     if (attr.type == cudaMemoryTypeManaged) return SPO_OK;
-    if (attr.type != cudaMemoryTypeDevice)
-        return spo_detail::fail(SPO_EINVAL, "%s must be device memory", name);
+    if (attr.type != cudaMemoryTypeDevice) return fail(SPO_EINVAL, "%s must be device memory", name);
     if (attr.device != device)
-        return spo_detail::fail(SPO_EINVAL, "%s lives on device %d, the set on device %d", name,
-                                attr.device, device);
+        return fail(SPO_EINVAL, "%s lives on device %d, the set on device %d", name, attr.device,
+                    device);
     return SPO_OK;
 }
 
 spo_status check_eval_args(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
                            const float *out) {
-    if (!set) return spo_detail::fail(SPO_EINVAL, "set is NULL");
-    if (!valid_kind(kind)) return spo_detail::fail(SPO_EINVAL, "invalid kind %d", (int)kind);
-    if (P < 0) return spo_detail::fail(SPO_EINVAL, "P = %lld is negative", (long long)P);
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    if (!valid_kind(kind)) return fail(SPO_EINVAL, "invalid kind %d", (int)kind);
+    if (P < 0) return fail(SPO_EINVAL, "P = %lld is negative", (long long)P);
     if (P == 0) return SPO_OK;
-    if (!pos || !out) return spo_detail::fail(SPO_EINVAL, "pos or out is NULL");
+    if (!pos || !out) return fail(SPO_EINVAL, "pos or out is NULL");
     const int64_t rows = spo_rows(kind);
-    // output elements must fit in int64 and the position count in a grid
     if (P > (INT64_C(1) << 40) / (rows * set->N))
-        return spo_detail::fail(SPO_EINVAL, "P = %lld too large for N = %lld", (long long)P,
-                                (long long)set->N);
+        return fail(SPO_EINVAL, "P = %lld too large for N = %lld", (long long)P, (long long)set->N);
+    return SPO_OK;
+}
+
+void free_workspace(spo_detail::Workspace &w) {
+    cudaFree(w.counts);
+    cudaFree(w.offsets);
+    cudaFree(w.keys);
+    cudaFree(w.slots);
+    cudaFree(w.perm);
+    w.counts = w.offsets = w.keys = w.slots = w.perm = nullptr;
+    w.cap_positions = w.cap_bins = 0;
+}
+
+// The scratch of `stream`, grown to hold P positions.  Caller holds set->mu.
+spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail::Workspace **out) {
+    spo_detail::Workspace *w = nullptr;
+    for (auto &x : s->ws)
+        if (x.stream == stream) w = &x;
+    if (!w) {
+        s->ws.emplace_back();
+        w = &s->ws.back();
+        w->stream = stream;
+    }
+    const int64_t nbins = (int64_t)s->nbx * s->nby * s->nbz;
+    if (w->cap_positions < P || w->cap_bins < nbins) {
+        const int64_t cp = std::max<int64_t>(P, w->cap_positions);
+        const int64_t cb = std::max<int64_t>(nbins, w->cap_bins);
+        free_workspace(*w);   // cudaFree waits for queued work that uses it
+        if (cudaMalloc(&w->counts, sizeof(int) * cb) != cudaSuccess ||
+            cudaMalloc(&w->offsets, sizeof(int) * (cb + 1)) != cudaSuccess ||
+            cudaMalloc(&w->keys, sizeof(int) * cp) != cudaSuccess ||
+            cudaMalloc(&w->slots, sizeof(int) * cp) != cudaSuccess ||
+            cudaMalloc(&w->perm, sizeof(int) * cp) != cudaSuccess) {
+            cudaGetLastError();
+            free_workspace(*w);
+            return fail(SPO_ENOMEM, "cudaMalloc of binning scratch for %lld positions failed",
+                        (long long)P);
+        }
+        w->cap_positions = cp;
+        w->cap_bins = cb;
+    }
+    *out = w;
+    return SPO_OK;
+}
+
+spo_algo choose_algo(const spo_set *s, int64_t P) {
+    const int64_t nbins = (int64_t)s->nbx * s->nby * s->nbz;
+    if (P >= INT_MAX || P < 1024) return SPO_ALGO_GATHER;
+    // a staged block pays off once a brick holds positions on average
+    if (s->has_block_map && P >= nbins) return SPO_ALGO_BRICK;
+    if (P >= 4 * nbins) return SPO_ALGO_SORTED_GATHER;
+    return SPO_ALGO_GATHER;
+}
+
+// Queue the binning of pos into the scratch of `stream`.  Caller holds set->mu.
+spo_status bin_queue(spo_set *s, const float *pos, int64_t P, cudaStream_t stream,
+                     spo_detail::Workspace **out) {
+    if (P >= INT_MAX) return fail(SPO_EINVAL, "binned strategies need P < 2^31");
+    spo_detail::Workspace *w = nullptr;
+    spo_status st = workspace_for(s, stream, P, &w);
+    if (st != SPO_OK) return st;
+    cudaError_t e = spo_detail::launch_bin(pos, P, s->nx, s->ny, s->nz, s->nbx, s->nby, s->nbz, *w,
+                                           stream);
+    if (e != cudaSuccess) {
+        w->binned_pos = nullptr;
+        w->binned_P = -1;
+        return cuda_fail(e, "binning launch");
+    }
+    w->binned_pos = pos;
+    w->binned_P = P;
+    *out = w;
+    return SPO_OK;
+}
+
+// Queue the evaluation stage of a binned strategy.  Caller holds set->mu.
+spo_status binned_eval_queue(const spo_set *s, spo_kind kind, const float *pos, int64_t P,
+                             float *out, cudaStream_t stream, spo_algo algo,
+                             const spo_detail::Workspace &w) {
+    cudaError_t e;
+    if (algo == SPO_ALGO_BRICK)
+        e = spo_detail::launch_brick(s->storage, kind, s, pos, w, P, out, stream);
+    else
+        e = spo_detail::launch_gather(s->storage, kind, spo_detail::view_of(s), pos, w.perm, P, out,
+                                      stream);
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "evaluation launch");
+}
+
+spo_status check_binned_algo(const spo_set *set, spo_algo algo) {
+    if (algo != SPO_ALGO_SORTED_GATHER && algo != SPO_ALGO_BRICK)
+        return fail(SPO_EINVAL, "invalid algo %d for a binned evaluation", (int)algo);
+    if (algo == SPO_ALGO_BRICK && !set->has_block_map)
+        return fail(SPO_EUNSUPPORTED, "the brick strategy needs at least 64 padded orbitals");
+    return SPO_OK;
+}
+
+// Queue one evaluation (arguments already checked; device already current).
+spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
+                      cudaStream_t stream, spo_algo algo) {
+    if (algo == SPO_ALGO_AUTO) algo = choose_algo(set, P);
+    if (algo == SPO_ALGO_GATHER) {
+        cudaError_t e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
+                                                  nullptr, P, out, stream);
+        return e == cudaSuccess ? SPO_OK : cuda_fail(e, "gather kernel launch");
+    }
+    spo_status st = check_binned_algo(set, algo);
+    if (st != SPO_OK) return st;
+    spo_set *s = const_cast<spo_set *>(set);
+    std::lock_guard<std::mutex> lock(s->mu);   // held until the launches are queued
+    spo_detail::Workspace *w = nullptr;
+    st = bin_queue(s, pos, P, stream, &w);
+    if (st != SPO_OK) return st;
+    return binned_eval_queue(s, kind, pos, P, out, stream, algo, *w);
+}
+
+// Common checks of the device-buffer entry points.
+spo_status check_device_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                             const float *out) {
+    spo_status s = check_eval_args(set, kind, pos, P, out);
+    if (s != SPO_OK || P == 0) return s;
+    if ((s = check_device_pointer(pos, set->device, "pos")) != SPO_OK) return s;
+    if ((s = check_device_pointer(out, set->device, "out")) != SPO_OK) return s;
+    if ((reinterpret_cast<uintptr_t>(pos) & 3) || (reinterpret_cast<uintptr_t>(out) & 3))
+        return fail(SPO_EINVAL, "pos and out must be 4-byte aligned");
     return SPO_OK;
 }
 
@@ -123,7 +247,6 @@ const char *spo_last_error(void) { return g_last_error; }
 
 spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dtype, int64_t N,
                       spo_dtype storage, int coefs_on_device, spo_set **out) {
-    using spo_detail::fail;
     g_last_error[0] = '\0';
     if (!out) return fail(SPO_EINVAL, "out is NULL");
     *out = nullptr;
@@ -132,8 +255,10 @@ spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dty
     if (grid->nx < 4 || grid->ny < 4 || grid->nz < 4)
         return fail(SPO_EINVAL, "grid %d x %d x %d: every n_d must be >= 4", grid->nx, grid->ny,
                     grid->nz);
-    const int64_t cells = (int64_t)grid->nx * grid->ny * grid->nz;
-    if (cells > INT32_MAX) return fail(SPO_EINVAL, "grid has more than 2^31-1 nodes");
+    if (grid->nx > (1 << 20) || grid->ny > (1 << 20) || grid->nz > (1 << 20))
+        return fail(SPO_EINVAL, "grid edge above 2^20");
+    const int64_t padded_rows = (int64_t)(grid->nx + 3) * (grid->ny + 3) * (grid->nz + 3);
+    if (padded_rows > INT32_MAX) return fail(SPO_EINVAL, "grid has more than 2^31-1 padded nodes");
     if (N < 1) return fail(SPO_EINVAL, "N = %lld must be >= 1", (long long)N);
     if (N > (INT64_C(1) << 24)) return fail(SPO_EINVAL, "N = %lld too large", (long long)N);
     if (dtype_size(src_dtype) == 0) return fail(SPO_EINVAL, "invalid src_dtype %d", (int)src_dtype);
@@ -156,10 +281,18 @@ spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dty
     set->nx = grid->nx;
     set->ny = grid->ny;
     set->nz = grid->nz;
+    set->xp = grid->nx + 3;
+    set->yp = grid->ny + 3;
+    set->zp = grid->nz + 3;
+    set->nbx = (grid->nx + spo_detail::kBrick - 1) / spo_detail::kBrick;
+    set->nby = (grid->ny + spo_detail::kBrick - 1) / spo_detail::kBrick;
+    set->nbz = (grid->nz + spo_detail::kBrick - 1) / spo_detail::kBrick;
     set->N = N;
     set->Np = (N + 7) / 8 * 8;
     set->storage = storage;
-    set->table_bytes = (size_t)cells * (size_t)set->Np * dtype_size(storage);
+    const size_t es = dtype_size(storage);
+    const size_t plane_bytes = (size_t)set->yp * set->zp * set->Np * es;
+    set->table_bytes = (size_t)set->xp * plane_bytes;
 
     e = cudaMalloc(&set->table, set->table_bytes);
     if (e != cudaSuccess) {
@@ -169,40 +302,53 @@ spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dty
         return fail(SPO_ENOMEM, "cudaMalloc of %zu table bytes failed", bytes);
     }
 
-    // convert in slabs of rows so that the staging buffer stays bounded
-    const size_t src_row_bytes = (size_t)N * dtype_size(src_dtype);
-    const int64_t slab_rows =
-        std::max<int64_t>(1, std::min<int64_t>(cells, (int64_t)((256u << 20) / src_row_bytes)));
+    // convert slabs of whole x-planes of the source (bounded staging memory)
+    const size_t src_plane = (size_t)grid->ny * grid->nz * N * dtype_size(src_dtype);
+    const int slab = (int)std::max<int64_t>(
+        1, std::min<int64_t>(grid->nx, (int64_t)((size_t)(512u << 20) / src_plane)));
     void *staging = nullptr;
     cudaStream_t stream = nullptr;
     spo_status status = SPO_OK;
     e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) status = cuda_fail(e, "cudaStreamCreate");
     if (status == SPO_OK && !coefs_on_device) {
-        e = cudaMalloc(&staging, (size_t)slab_rows * src_row_bytes);
+        e = cudaMalloc(&staging, (size_t)slab * src_plane);
         if (e != cudaSuccess) {
             cudaGetLastError();
             status = fail(SPO_ENOMEM, "cudaMalloc of the upload staging buffer failed");
         }
     }
-    for (int64_t r0 = 0; status == SPO_OK && r0 < cells; r0 += slab_rows) {
-        const int64_t nrows = std::min<int64_t>(slab_rows, cells - r0);
-        const char *src = static_cast<const char *>(coefs) + (size_t)r0 * src_row_bytes;
+    for (int x0 = 0; status == SPO_OK && x0 < grid->nx; x0 += slab) {
+        const int x1 = std::min(grid->nx, x0 + slab);
+        const char *src = static_cast<const char *>(coefs) + (size_t)x0 * src_plane;
         if (!coefs_on_device) {
-            e = cudaMemcpyAsync(staging, src, (size_t)nrows * src_row_bytes,
-                                cudaMemcpyHostToDevice, stream);
+            e = cudaMemcpyAsync(staging, src, (size_t)(x1 - x0) * src_plane, cudaMemcpyHostToDevice,
+                                stream);
             if (e != cudaSuccess) { status = cuda_fail(e, "upload of coefficients"); break; }
             src = static_cast<const char *>(staging);
         }
-        char *dst = static_cast<char *>(set->table) + (size_t)r0 * set->Np * dtype_size(storage);
-        e = spo_detail::launch_convert(src, src_dtype, dst, storage, nrows, N, set->Np, stream);
+        e = spo_detail::launch_convert(src, src_dtype, x0, x1, set, stream);
         if (e != cudaSuccess) { status = cuda_fail(e, "conversion kernel"); break; }
-        // the staging buffer is reused by the next slab
-        e = cudaStreamSynchronize(stream);
+        e = cudaStreamSynchronize(stream);   // the staging buffer is reused
         if (e != cudaSuccess) { status = cuda_fail(e, "conversion"); break; }
+    }
+    // ghost x-planes: padded 0 <- node nx-1 (padded nx), nx+1 <- node 0, nx+2 <- node 1
+    const int ghost_src[3] = {grid->nx, 1, 2};
+    const int ghost_dst[3] = {0, grid->nx + 1, grid->nx + 2};
+    for (int g = 0; status == SPO_OK && g < 3; ++g) {
+        char *base = static_cast<char *>(set->table);
+        e = cudaMemcpyAsync(base + (size_t)ghost_dst[g] * plane_bytes,
+                            base + (size_t)ghost_src[g] * plane_bytes, plane_bytes,
+                            cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) status = cuda_fail(e, "ghost plane copy");
+    }
+    if (status == SPO_OK) {
+        e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) status = cuda_fail(e, "table upload");
     }
     if (staging) cudaFree(staging);
     if (stream) cudaStreamDestroy(stream);
+    if (status == SPO_OK) status = spo_detail::make_block_map(set);
     if (status != SPO_OK) {
         cudaFree(set->table);
         delete set;
@@ -216,6 +362,7 @@ spo_status spo_destroy(spo_set *set) {
     if (!set) return SPO_OK;
     DeviceGuard guard(set->device);
     cudaDeviceSynchronize();
+    for (auto &w : set->ws) free_workspace(w);
     for (int i = 0; i < 2; ++i) {
         if (set->hpos[i]) cudaFree(set->hpos[i]);
         if (set->hout[i]) cudaFree(set->hout[i]);
@@ -227,20 +374,58 @@ spo_status spo_destroy(spo_set *set) {
     return e == cudaSuccess ? SPO_OK : cuda_fail(e, "cudaFree of the table");
 }
 
+spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
+                       void *stream, spo_algo algo) {
+    g_last_error[0] = '\0';
+    if (algo < SPO_ALGO_AUTO || algo > SPO_ALGO_BRICK)
+        return fail(SPO_EINVAL, "invalid algo %d", (int)algo);
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    DeviceGuard guard(set->device);
+    if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+    spo_status s = check_device_eval(set, kind, pos, P, out);
+    if (s != SPO_OK || P == 0) return s;
+    return eval_queue(set, kind, pos, P, out, static_cast<cudaStream_t>(stream), algo);
+}
+
+spo_status spo_bin(const spo_set *set, const float *pos, int64_t P, void *stream) {
+    g_last_error[0] = '\0';
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    if (P < 0) return fail(SPO_EINVAL, "P = %lld is negative", (long long)P);
+    if (P > 0 && !pos) return fail(SPO_EINVAL, "pos is NULL");
+    DeviceGuard guard(set->device);
+    if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+    spo_status st;
+    if (P > 0 && (st = check_device_pointer(pos, set->device, "pos")) != SPO_OK) return st;
+    spo_set *s = const_cast<spo_set *>(set);
+    std::lock_guard<std::mutex> lock(s->mu);
+    spo_detail::Workspace *w = nullptr;
+    return bin_queue(s, pos, P, static_cast<cudaStream_t>(stream), &w);
+}
+
+spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                           float *out, void *stream, spo_algo algo) {
+    g_last_error[0] = '\0';
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    DeviceGuard guard(set->device);
+    if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+    spo_status st = check_device_eval(set, kind, pos, P, out);
+    if (st != SPO_OK || P == 0) return st;
+    if ((st = check_binned_algo(set, algo)) != SPO_OK) return st;
+    spo_set *s = const_cast<spo_set *>(set);
+    std::lock_guard<std::mutex> lock(s->mu);
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    for (auto &w : s->ws)
+        if (w.stream == cs) {
+            if (w.binned_pos != pos || w.binned_P != P)
+                return fail(SPO_EINVAL, "pos/P differ from the last spo_bin on this stream");
+            return binned_eval_queue(s, kind, pos, P, out, cs, algo, w);
+        }
+    return fail(SPO_EINVAL, "no spo_bin on this stream for this set");
+}
+
 spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
                     void *stream) {
-    g_last_error[0] = '\0';
-    spo_status s = check_eval_args(set, kind, pos, P, out);
-    if (s != SPO_OK || P == 0) return s;
-    DeviceGuard guard(set->device);
-    if (!guard.ok()) return spo_detail::fail(SPO_ECUDA, "cannot select device %d", set->device);
-    if ((s = check_device_pointer(pos, set->device, "pos")) != SPO_OK) return s;
-    if ((s = check_device_pointer(out, set->device, "out")) != SPO_OK) return s;
-    if ((reinterpret_cast<uintptr_t>(pos) & 3) || (reinterpret_cast<uintptr_t>(out) & 3))
-        return spo_detail::fail(SPO_EINVAL, "pos and out must be 4-byte aligned");
-    spo_detail::EvalArgs a{set->table, set->nx, set->ny, set->nz, set->N, set->Np, pos, P, out};
-    cudaError_t e = spo_detail::launch_eval(set->storage, kind, a, static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "evaluation launch");
+    return spo_eval_ex(set, kind, pos, P, out, stream, SPO_ALGO_AUTO);
 }
 
 spo_status spo_eval_v(const spo_set *set, const float *pos, int64_t P, float *out, void *stream) {
@@ -255,9 +440,27 @@ spo_status spo_eval_vgh(const spo_set *set, const float *pos, int64_t P, float *
     return spo_eval(set, SPO_KIND_VGH, pos, P, out, stream);
 }
 
+spo_status spo_reserve(spo_set *set, int64_t P, void *stream) {
+    g_last_error[0] = '\0';
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    if (P < 0 || P >= INT_MAX) return fail(SPO_EINVAL, "P = %lld out of range", (long long)P);
+    DeviceGuard guard(set->device);
+    if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+    std::lock_guard<std::mutex> lock(set->mu);
+    spo_detail::Workspace *w = nullptr;
+    return workspace_for(set, static_cast<cudaStream_t>(stream), std::max<int64_t>(P, 1), &w);
+}
+
+spo_status spo_device_status(unsigned int *flags, int clear, void *stream) {
+    g_last_error[0] = '\0';
+    if (!flags) return fail(SPO_EINVAL, "flags is NULL");
+    cudaError_t e = spo_detail::read_device_status(flags, clear != 0, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "device status read");
+    return (*flags & 1u) ? fail(SPO_ETIMEOUT, "a bounded wait on a TMA copy gave up") : SPO_OK;
+}
+
 spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
                          float *out_host, void *stream) {
-    using spo_detail::fail;
     g_last_error[0] = '\0';
     spo_status s = check_eval_args(set, kind, pos_host, P, out_host);
     if (s != SPO_OK || P == 0) return s;
@@ -266,8 +469,11 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
 
     const int64_t rows = spo_rows(kind);
     const size_t out_row = (size_t)rows * (size_t)set->N * sizeof(float);   // per position
-    // chunks of about 64 MB of output, at least 256 positions
-    const int64_t chunk = std::min<int64_t>(P, std::max<int64_t>(256, (int64_t)((64u << 20) / out_row)));
+    // about four chunks per batch (copies of one overlap the kernel of the
+    // next), at most 512 MB of output per chunk, at least 256 positions
+    int64_t chunk = std::max<int64_t>((P + 3) / 4, 256);
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(256, (int64_t)((size_t)(512u << 20) / out_row)));
+    chunk = std::min<int64_t>(chunk, P);
     const size_t need_pos = (size_t)chunk * 3 * sizeof(float);
     const size_t need_out = (size_t)chunk * out_row;
     cudaError_t e;
@@ -280,25 +486,24 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
             e = cudaEventCreateWithFlags(&set->hevent[i], cudaEventDisableTiming);
             if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
         }
-        if (set->hpos_cap < need_pos || set->hout_cap < need_out) {
-            // grow both buffers of both streams
-            for (int j = 0; j < 2; ++j) {
-                if (set->hstream[j]) cudaStreamSynchronize(set->hstream[j]);
-                if (set->hpos[j]) cudaFree(set->hpos[j]);
-                if (set->hout[j]) cudaFree(set->hout[j]);
-                set->hpos[j] = set->hout[j] = nullptr;
-            }
-            set->hpos_cap = set->hout_cap = 0;
-            for (int j = 0; j < 2; ++j) {
-                if (cudaMalloc(&set->hpos[j], need_pos) != cudaSuccess ||
-                    cudaMalloc(&set->hout[j], need_out) != cudaSuccess) {
-                    cudaGetLastError();
-                    return fail(SPO_ENOMEM, "cudaMalloc of %zu staging bytes failed", need_out);
-                }
-            }
-            set->hpos_cap = need_pos;
-            set->hout_cap = need_out;
+    }
+    if (set->hpos_cap < need_pos || set->hout_cap < need_out) {
+        for (int j = 0; j < 2; ++j) {
+            cudaStreamSynchronize(set->hstream[j]);
+            if (set->hpos[j]) cudaFree(set->hpos[j]);
+            if (set->hout[j]) cudaFree(set->hout[j]);
+            set->hpos[j] = set->hout[j] = nullptr;
         }
+        set->hpos_cap = set->hout_cap = 0;
+        for (int j = 0; j < 2; ++j) {
+            if (cudaMalloc(&set->hpos[j], need_pos) != cudaSuccess ||
+                cudaMalloc(&set->hout[j], need_out) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(SPO_ENOMEM, "cudaMalloc of %zu staging bytes failed", need_out);
+            }
+        }
+        set->hpos_cap = need_pos;
+        set->hout_cap = need_out;
     }
     // order after the caller's stream
     cudaEvent_t start;
@@ -316,10 +521,8 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
         e = cudaMemcpyAsync(set->hpos[i], pos_host + 3 * p0, (size_t)np * 3 * sizeof(float),
                             cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { status = cuda_fail(e, "position upload"); break; }
-        spo_detail::EvalArgs a{set->table, set->nx, set->ny, set->nz, set->N, set->Np,
-                               set->hpos[i], np, set->hout[i]};
-        e = spo_detail::launch_eval(set->storage, kind, a, st);
-        if (e != cudaSuccess) { status = cuda_fail(e, "evaluation launch"); break; }
+        status = eval_queue(set, kind, set->hpos[i], np, set->hout[i], st, SPO_ALGO_AUTO);
+        if (status != SPO_OK) break;
         e = cudaMemcpyAsync(reinterpret_cast<char *>(out_host) + (size_t)p0 * out_row, set->hout[i],
                             (size_t)np * out_row, cudaMemcpyDeviceToHost, st);
         if (e != cudaSuccess) { status = cuda_fail(e, "output download"); break; }
@@ -333,14 +536,14 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
 }
 
 spo_status spo_footprint(const spo_set *set, size_t *bytes) {
-    if (!set || !bytes) return spo_detail::fail(SPO_EINVAL, "set or bytes is NULL");
+    if (!set || !bytes) return fail(SPO_EINVAL, "set or bytes is NULL");
     *bytes = set->table_bytes;
     return SPO_OK;
 }
 
 spo_status spo_info(const spo_set *set, spo_grid *grid, int64_t *N, int64_t *Np,
                     spo_dtype *storage) {
-    if (!set) return spo_detail::fail(SPO_EINVAL, "set is NULL");
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
     if (grid) *grid = spo_grid{set->nx, set->ny, set->nz};
     if (N) *N = set->N;
     if (Np) *Np = set->Np;

@@ -1,0 +1,117 @@
+// Binning of positions by brick (a counting sort), so that the brick kernel
+// can evaluate all positions whose windows lie in one staged block of the
+// table, and the gather kernel can visit positions in spatial order.
+//
+//   1. bin_count_kernel:  key = brick of the position's cell; slot = rank of
+//                         the position within its brick (atomic counter)
+//   2. bin_scan_kernel:   offsets = exclusive prefix sum of the counts
+//   3. bin_scatter_kernel: perm[offsets[key] + slot] = position index
+//
+// The order inside a brick depends on atomic arrival order; every output of
+// a position depends only on that position, so results are unaffected.
+#include "spo_device.cuh"
+#include "spo_internal.h"
+
+namespace {
+
+using namespace spo_dev;
+using spo_detail::kBrick;
+
+__global__ void bin_count_kernel(const float *__restrict__ pos, int64_t P, int nx, int ny, int nz,
+                                 int nby, int nbz, int *__restrict__ counts, int *__restrict__ keys,
+                                 int *__restrict__ slots) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        int cx, cy, cz;
+        float t;
+        reduce_axis(__ldg(pos + 3 * p + 0), nx, cx, t);
+        reduce_axis(__ldg(pos + 3 * p + 1), ny, cy, t);
+        reduce_axis(__ldg(pos + 3 * p + 2), nz, cz, t);
+        const int key = ((cx / kBrick) * nby + cy / kBrick) * nbz + cz / kBrick;
+        keys[p] = key;
+        slots[p] = atomicAdd(counts + key, 1);
+    }
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+
+// Exclusive scan of counts[0..n) into offsets[0..n]; one block, looping over
+// chunks of kScanThreads * kScanItems with a running carry.
+__global__ void __launch_bounds__(kScanThreads)
+bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int n) {
+    __shared__ int warp_sums[kScanThreads / 32];
+    __shared__ int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += kScanThreads * kScanItems) {
+        int v[kScanItems];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int i = base + tid * kScanItems + k;
+            v[k] = i < n ? counts[i] : 0;
+            sum += v[k];
+        }
+        // inclusive scan of the per-thread sums within the warp
+        int incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = warp_sums[lane];
+            int wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, d);
+                if (lane >= d) wi += y;
+            }
+            warp_sums[lane] = wi - w;   // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        int run = carry + warp_sums[warp] + incl - sum;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int i = base + tid * kScanItems + k;
+            if (i < n) offsets[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == kScanThreads - 1) carry_s = run;   // last thread holds the chunk total
+        __syncthreads();
+    }
+    if (tid == 0) offsets[n] = carry_s;
+}
+
+__global__ void bin_scatter_kernel(const int *__restrict__ keys, const int *__restrict__ slots,
+                                   const int *__restrict__ offsets, int *__restrict__ perm, int64_t P) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * blockDim.x)
+        perm[offsets[keys[p]] + slots[p]] = (int)p;
+}
+
+}  // namespace
+
+namespace spo_detail {
+
+cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int nbx, int nby,
+                       int nbz, Workspace &w, cudaStream_t stream) {
+    const int nbins = nbx * nby * nbz;
+    cudaError_t e = cudaMemsetAsync(w.counts, 0, sizeof(int) * (size_t)nbins, stream);
+    if (e != cudaSuccess) return e;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((P + threads - 1) / threads, 152 * 16);
+    bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, nx, ny, nz, nby, nbz, w.counts, w.keys,
+                                                     w.slots);
+    bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(w.counts, w.offsets, nbins);
+    bin_scatter_kernel<<<blocks, threads, 0, stream>>>(w.keys, w.slots, w.offsets, w.perm, P);
+    return cudaGetLastError();
+}
+
+}  // namespace spo_detail

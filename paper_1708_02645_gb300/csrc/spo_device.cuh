@@ -1,0 +1,257 @@
+// Device helpers shared by the evaluation kernels: coordinate reduction,
+// cubic B-spline weights, widening loads and the z -> y -> x reduction of one
+// 4x4x4 window for V consecutive orbitals.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "spo.h"
+
+namespace spo_dev {
+
+template <int KIND>
+struct Rows {
+    static constexpr int value = KIND == SPO_KIND_V ? 1 : (KIND == SPO_KIND_VGL ? 5 : 10);
+};
+
+// ---------------------------------------------------------------------------
+// widening loads of V = 2 or 4 consecutive coefficients (global memory via
+// the read-only path, or shared memory)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void bf16x2(uint32_t r, float *v) {
+    // a bf16 is the upper half of the FP32 with the same value
+    v[0] = __uint_as_float(r << 16);
+    v[1] = __uint_as_float(r & 0xffff0000u);
+}
+
+__device__ __forceinline__ void f16x2(uint32_t r, float *v) {
+    __half2 h;
+    memcpy(&h, &r, 4);
+    const float2 f = __half22float2(h);
+    v[0] = f.x;
+    v[1] = f.y;
+}
+
+template <bool GLOBAL, typename W>
+__device__ __forceinline__ W fetch(const void *p) {
+    if constexpr (GLOBAL) return __ldg(reinterpret_cast<const W *>(p));
+    else return *reinterpret_cast<const W *>(p);
+}
+
+template <typename T, int V, bool GLOBAL>
+__device__ __forceinline__ void load_coefs(const T *p, float *v) {
+    static_assert(V == 2 || V == 4, "2 or 4 orbitals per thread");
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (V == 4) {
+            const float4 r = fetch<GLOBAL, float4>(p);
+            v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
+        } else {
+            const float2 r = fetch<GLOBAL, float2>(p);
+            v[0] = r.x; v[1] = r.y;
+        }
+    } else {
+        constexpr bool BF = std::is_same<T, __nv_bfloat16>::value;
+        if constexpr (V == 4) {
+            const uint2 r = fetch<GLOBAL, uint2>(p);
+            if constexpr (BF) { bf16x2(r.x, v); bf16x2(r.y, v + 2); }
+            else { f16x2(r.x, v); f16x2(r.y, v + 2); }
+        } else {
+            const uint32_t r = fetch<GLOBAL, uint32_t>(p);
+            if constexpr (BF) bf16x2(r, v);
+            else f16x2(r, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-position geometry
+// ---------------------------------------------------------------------------
+
+// Cell index i in [0, n) and fraction t in [0, 1] of coordinate r on a
+// periodic axis of n intervals.  t = r*n - floor(r*n) is formed with one
+// fused multiply-add, so it is the FP32 rounding of the exact fraction.
+// NaN or Inf coordinates end in cell 0 with t = 0.
+__device__ __forceinline__ void reduce_axis(float r, int n, int &cell, float &t) {
+    const float fn = (float)n;
+    float fl = floorf(r * fn);
+    float tt = fmaf(r, fn, -fl);
+    if (tt < 0.0f) {
+        fl -= 1.0f;
+        tt += 1.0f;
+    } else if (tt >= 1.0f) {
+        fl += 1.0f;
+        tt -= 1.0f;
+    }
+    if (!(tt >= 0.0f && tt <= 1.0f)) tt = 0.0f;
+    fl = fminf(fmaxf(fl, -1.0e9f), 1.0e9f);   // fmaxf maps NaN to the bound
+    int c = (int)fl % n;
+    if (c < 0) c += n;
+    cell = c;
+    t = tt;
+}
+
+// Cubic B-spline weights of the four window nodes (i-1, i, i+1, i+2) at
+// fraction t, with first and second derivatives scaled to d/dr (factors n
+// and n^2).
+struct Axis {
+    float w[4], d[4], dd[4];
+    int cell;
+};
+
+__device__ __forceinline__ void make_axis(float r, int n, Axis &ax) {
+    float t;
+    reduce_axis(r, n, ax.cell, t);
+    const float fn = (float)n, fn2 = fn * fn;
+    const float s = 1.0f - t, t2 = t * t, s2 = s * s;
+    ax.w[0] = (1.0f / 6.0f) * s2 * s;
+    ax.w[1] = fmaf(t2, fmaf(0.5f, t, -1.0f), 2.0f / 3.0f);
+    ax.w[2] = fmaf(fmaf(fmaf(-0.5f, t, 0.5f), t, 0.5f), t, 1.0f / 6.0f);
+    ax.w[3] = (1.0f / 6.0f) * t2 * t;
+    ax.d[0] = -0.5f * s2 * fn;
+    ax.d[1] = fmaf(1.5f, t, -2.0f) * t * fn;
+    ax.d[2] = fmaf(fmaf(-1.5f, t, 1.0f), t, 0.5f) * fn;
+    ax.d[3] = 0.5f * t2 * fn;
+    ax.dd[0] = s * fn2;
+    ax.dd[1] = fmaf(3.0f, t, -2.0f) * fn2;
+    ax.dd[2] = fmaf(-3.0f, t, 1.0f) * fn2;
+    ax.dd[3] = t * fn2;
+}
+
+// ---------------------------------------------------------------------------
+// the window reduction
+// ---------------------------------------------------------------------------
+// acc[NC][V] += the terms of x node a (weights xw, xd, xdd) of one window,
+// for V consecutive orbitals.  load(a, b, g, v) fetches the V coefficients
+// of corner (a, b, g).  The order of every FMA is fixed here, so all kernels
+// produce the same bits for the same position and orbitals.
+template <int KIND, int V, typename Load>
+__device__ __forceinline__ void window_x_node(int a, float xw, float xd, float xdd, const Axis &Y,
+                                              const Axis &Z, Load &load,
+                                              float (&acc)[Rows<KIND>::value][V]) {
+    constexpr int NY = KIND == SPO_KIND_V ? 1 : (KIND == SPO_KIND_VGL ? 5 : 6);
+    // y-stage partial sums for this x node
+    //   VGH: wy*v, dy*v, ddy*v, wy*dz, dy*dz, wy*ddz
+    //   VGL: wy*v, dy*v, ddy*v, wy*dz, wy*ddz
+    //   V:   wy*v
+    float ys[NY][V];
+#pragma unroll
+    for (int j = 0; j < NY; ++j)
+#pragma unroll
+        for (int k = 0; k < V; ++k) ys[j][k] = 0.0f;
+
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float cv[4][V];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) load(a, b, g, cv[g]);
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            float zv = Z.w[0] * cv[0][k];
+            zv = fmaf(Z.w[1], cv[1][k], zv);
+            zv = fmaf(Z.w[2], cv[2][k], zv);
+            zv = fmaf(Z.w[3], cv[3][k], zv);
+            ys[0][k] = fmaf(Y.w[b], zv, ys[0][k]);
+            if constexpr (KIND != SPO_KIND_V) {
+                float zd = Z.d[0] * cv[0][k];
+                zd = fmaf(Z.d[1], cv[1][k], zd);
+                zd = fmaf(Z.d[2], cv[2][k], zd);
+                zd = fmaf(Z.d[3], cv[3][k], zd);
+                float zdd = Z.dd[0] * cv[0][k];
+                zdd = fmaf(Z.dd[1], cv[1][k], zdd);
+                zdd = fmaf(Z.dd[2], cv[2][k], zdd);
+                zdd = fmaf(Z.dd[3], cv[3][k], zdd);
+                ys[1][k] = fmaf(Y.d[b], zv, ys[1][k]);
+                ys[2][k] = fmaf(Y.dd[b], zv, ys[2][k]);
+                ys[3][k] = fmaf(Y.w[b], zd, ys[3][k]);
+                if constexpr (KIND == SPO_KIND_VGH) {
+                    ys[4][k] = fmaf(Y.d[b], zd, ys[4][k]);
+                    ys[5][k] = fmaf(Y.w[b], zdd, ys[5][k]);
+                } else {
+                    ys[4][k] = fmaf(Y.w[b], zdd, ys[4][k]);
+                }
+            }
+        }
+    }
+    // x stage
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        acc[0][k] = fmaf(xw, ys[0][k], acc[0][k]);                 // v
+        if constexpr (KIND == SPO_KIND_VGH) {
+            acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);             // gx
+            acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);             // gy
+            acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);             // gz
+            acc[4][k] = fmaf(xdd, ys[0][k], acc[4][k]);            // hxx
+            acc[5][k] = fmaf(xd, ys[1][k], acc[5][k]);             // hxy
+            acc[6][k] = fmaf(xd, ys[3][k], acc[6][k]);             // hxz
+            acc[7][k] = fmaf(xw, ys[2][k], acc[7][k]);             // hyy
+            acc[8][k] = fmaf(xw, ys[4][k], acc[8][k]);             // hyz
+            acc[9][k] = fmaf(xw, ys[5][k], acc[9][k]);             // hzz
+        } else if constexpr (KIND == SPO_KIND_VGL) {
+            acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);             // gx
+            acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);             // gy
+            acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);             // gz
+            // lap = hxx + hyy + hzz
+            float l = fmaf(xdd, ys[0][k], acc[4][k]);
+            l = fmaf(xw, ys[2][k], l);
+            acc[4][k] = fmaf(xw, ys[4][k], l);
+        }
+    }
+}
+
+// acc[NC][V] += the 64-term sums of one window (x nodes a = 0..3 in order).
+// UNROLL_A unrolls the x-node loop (all 64 loads visible to the scheduler,
+// for latency hiding on global loads); otherwise the loop stays rolled and
+// the x weights rotate through registers, which keeps only one x node's 16
+// loads live (for short-latency shared loads under a register cap).
+template <int KIND, int V, bool UNROLL_A, typename Load>
+__device__ __forceinline__ void window_reduce(const Axis &X, const Axis &Y, const Axis &Z,
+                                              Load load, float (&acc)[Rows<KIND>::value][V]) {
+    if constexpr (UNROLL_A) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            window_x_node<KIND, V>(a, X.w[a], X.d[a], X.dd[a], Y, Z, load, acc);
+    } else {
+        float w0 = X.w[0], w1 = X.w[1], w2 = X.w[2], w3 = X.w[3];
+        float d0 = X.d[0], d1 = X.d[1], d2 = X.d[2], d3 = X.d[3];
+        float e0 = X.dd[0], e1 = X.dd[1], e2 = X.dd[2], e3 = X.dd[3];
+#pragma unroll 1
+        for (int a = 0; a < 4; ++a) {
+            window_x_node<KIND, V>(a, w0, d0, e0, Y, Z, load, acc);
+            w0 = w1; w1 = w2; w2 = w3;
+            d0 = d1; d1 = d2; d2 = d3;
+            e0 = e1; e1 = e2; e2 = e3;
+        }
+    }
+}
+
+// Streaming store of the NC x V results of one thread; o points at this
+// thread's first orbital in component 0 of one position, N is the row
+// stride, `left` orbitals remain in the row from that first orbital.  With
+// VEC_OUT, V values go out as one 8- or 16-byte store per component (the
+// caller guarantees alignment and N % V == 0).
+template <int NC, int V, bool VEC_OUT>
+__device__ __forceinline__ void store_rows(float *o, int64_t N, int64_t left,
+                                           const float (&acc)[NC][V]) {
+    if constexpr (VEC_OUT) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if constexpr (V == 4)
+                __stcs(reinterpret_cast<float4 *>(o + c * N),
+                       make_float4(acc[c][0], acc[c][1], acc[c][2], acc[c][3]));
+            else
+                __stcs(reinterpret_cast<float2 *>(o + c * N), make_float2(acc[c][0], acc[c][1]));
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k < left) __stcs(o + c * N + k, acc[c][k]);
+    }
+}
+
+}  // namespace spo_dev

@@ -1,20 +1,58 @@
-// Internal declarations shared by the host API (spo_api.cu) and the kernels
-// (spo_eval.cu).  Not part of the C ABI.
+// Internal declarations shared by the host API and the kernels.  Not part of
+// the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <vector>
+
 #include "spo.h"
+
+namespace spo_detail {
+
+// Edge of a brick in cells: positions are binned by brick, and the brick
+// kernel stages the (kBrick + 3)^3 table rows a brick's windows touch.
+constexpr int kBrick = 4;
+constexpr int kBlockEdge = kBrick + 3;
+
+// Scratch of the binned path for one stream: brick counts and offsets, one
+// key and slot per position, and the position permutation sorted by brick.
+struct Workspace {
+    cudaStream_t stream = nullptr;
+    int *counts = nullptr;    // [nbins]
+    int *offsets = nullptr;   // [nbins + 1]
+    int *keys = nullptr;      // [P]
+    int *slots = nullptr;     // [P]
+    int *perm = nullptr;      // [P]
+    int64_t cap_positions = 0;
+    int64_t cap_bins = 0;
+    const float *binned_pos = nullptr;   // positions of the last binning
+    int64_t binned_P = -1;
+};
+
+}  // namespace spo_detail
 
 struct spo_set {
     int device = 0;
-    int nx = 0, ny = 0, nz = 0;
-    int64_t N = 0;     // orbitals
-    int64_t Np = 0;    // padded orbital stride of the table (multiple of 8)
+    int nx = 0, ny = 0, nz = 0;            // grid intervals
+    int xp = 0, yp = 0, zp = 0;            // padded node counts, n + 3
+    int nbx = 0, nby = 0, nbz = 0;         // bricks per axis
+    int64_t N = 0;      // orbitals
+    int64_t Np = 0;     // padded orbital stride of the table (multiple of 8)
     spo_dtype storage = SPO_F32;
-    void *table = nullptr;       // [nx][ny][nz][Np] of the storage type
+    void *table = nullptr;   // [xp][yp][zp][Np] of the storage type; padded node
+                             // i' holds grid node (i' - 1) mod n
     size_t table_bytes = 0;
+    int tile = 0;            // orbitals per brick-kernel tile
+    CUtensorMap block_map;   // 4-D TMA map of the table, box (tile, 7, 7, 7)
+    bool has_block_map = false;
+
+    // scratch of the binned path, one per stream (guarded by mu)
+    std::mutex mu;
+    std::vector<spo_detail::Workspace> ws;
 
     // staging for spo_eval_host: two streams, each with its own device
     // buffers for one chunk of positions and outputs
@@ -30,23 +68,43 @@ namespace spo_detail {
 // Records a formatted message for spo_last_error() and returns `status`.
 spo_status fail(spo_status status, const char *fmt, ...);
 
-// Arguments of one evaluation launch.
-struct EvalArgs {
+// Geometry of one table as the kernels see it.
+struct TableView {
     const void *table;
-    int nx, ny, nz;
+    int nx, ny, nz;      // intervals
+    int yp, zp;          // padded node counts (y, z)
     int64_t N, Np;
-    const float *pos;   // [P][3]
-    int64_t P;
-    float *out;         // [P][rows][N]
 };
 
-// Queue the evaluation kernel for `kind` on `stream`.  P must be > 0.
-cudaError_t launch_eval(spo_dtype storage, spo_kind kind, const EvalArgs &args,
-                        cudaStream_t stream);
+inline TableView view_of(const spo_set *s) {
+    return TableView{s->table, s->nx, s->ny, s->nz, s->yp, s->zp, s->N, s->Np};
+}
 
-// Convert `rows` rows of `N` source coefficients (src_dtype, row stride N)
-// into the table layout (storage, row stride Np, zero padding).
-cudaError_t launch_convert(const void *src, spo_dtype src_dtype, void *dst, spo_dtype storage,
-                           int64_t rows, int64_t N, int64_t Np, cudaStream_t stream);
+// Gather kernel: one thread = 4 orbitals of one position, corner rows read
+// straight from global memory.  perm == nullptr evaluates positions in
+// order; otherwise thread-group i evaluates position perm[i].
+cudaError_t launch_gather(spo_dtype storage, spo_kind kind, const TableView &t,
+                          const float *pos, const int *perm, int64_t P, float *out,
+                          cudaStream_t stream);
+
+// Binning: counts/keys/slots, exclusive scan into offsets, permutation.
+cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int nbx, int nby,
+                       int nbz, Workspace &w, cudaStream_t stream);
+
+// Brick kernel over all (brick, orbital tile) items of a binned batch.
+cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set,
+                         const float *pos, const Workspace &w, int64_t P, float *out,
+                         cudaStream_t stream);
+
+// Convert the source coefficients of grid x-planes [x0, x1) (src_dtype,
+// [x1-x0][ny][nz][N]) into every padded table row that holds one of them.
+cudaError_t launch_convert(const void *src, spo_dtype src_dtype, int x0, int x1,
+                           const spo_set *set, cudaStream_t stream);
+
+// Build the brick kernel's tensor map for a set (host; driver entry point).
+spo_status make_block_map(spo_set *set);
+
+// Device-side error word (bounded waits that gave up); read and clear.
+cudaError_t read_device_status(unsigned int *flags, bool clear, cudaStream_t stream);
 
 }  // namespace spo_detail

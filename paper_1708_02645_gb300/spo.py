@@ -19,6 +19,9 @@ F64, F32, BF16, F16 = 0, 1, 2, 3
 DTYPES = {"f64": F64, "f32": F32, "bf16": BF16, "f16": F16}
 KIND_V, KIND_VGL, KIND_VGH = 0, 1, 2
 KINDS = {"v": KIND_V, "vgl": KIND_VGL, "vgh": KIND_VGH}
+ALGO_AUTO, ALGO_GATHER, ALGO_SORTED_GATHER, ALGO_BRICK = 0, 1, 2, 3
+ALGOS = {"auto": ALGO_AUTO, "gather": ALGO_GATHER, "sorted_gather": ALGO_SORTED_GATHER,
+         "brick": ALGO_BRICK}
 ROWS = {KIND_V: 1, KIND_VGL: 5, KIND_VGH: 10}
 STATUS = {0: "SPO_OK", 1: "SPO_EINVAL", 2: "SPO_ENOMEM", 3: "SPO_ECUDA", 4: "SPO_ETIMEOUT",
           5: "SPO_EUNSUPPORTED"}
@@ -34,6 +37,11 @@ SIGNATURES = [
     ("spo_eval_vgl", _INT, [_P, _P, _I64, _P, _P]),
     ("spo_eval_vgh", _INT, [_P, _P, _I64, _P, _P]),
     ("spo_eval", _INT, [_P, _INT, _P, _I64, _P, _P]),
+    ("spo_eval_ex", _INT, [_P, _INT, _P, _I64, _P, _P, _INT]),
+    ("spo_bin", _INT, [_P, _P, _I64, _P]),
+    ("spo_eval_binned", _INT, [_P, _INT, _P, _I64, _P, _P, _INT]),
+    ("spo_reserve", _INT, [_P, _I64, _P]),
+    ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
@@ -117,6 +125,15 @@ def _dtype_of(coefs, src_dtype):
     return m[coefs.dtype]
 
 
+def device_status(clear: bool = True, stream=None) -> int:
+    """Device-side status word of the current device (bit 0: a bounded wait
+    on a TMA copy gave up).  Raises SpoError(SPO_ETIMEOUT) if bit 0 is set."""
+    flags = ctypes.c_uint()
+    _check(load().spo_device_status(ctypes.byref(flags), int(clear), _stream_handle(stream)),
+           "spo_device_status")
+    return int(flags.value)
+
+
 class OrbitalSet:
     """One B-spline orbital set resident on the current CUDA device.
 
@@ -173,24 +190,56 @@ class OrbitalSet:
         k = KINDS[kind] if isinstance(kind, str) else int(kind)
         return (P, self.N) if k == KIND_V else (P, ROWS[k], self.N)
 
-    def eval(self, pos, kind="vgh", out=None, stream=None):
-        """Evaluate at device positions pos [P, 3] (FP32 torch CUDA tensor).
-        Returns out (allocated if None): [P, N], [P, 5, N] or [P, 10, N]."""
+    def _check_pos(self, pos):
         torch = _torch()
-        k = KINDS[kind] if isinstance(kind, str) else int(kind)
         if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dtype == torch.float32):
             raise TypeError("pos must be a float32 CUDA tensor")
         if pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
             raise ValueError("pos must be a contiguous [P, 3] tensor")
-        P = int(pos.shape[0])
+        return int(pos.shape[0])
+
+    def _out_for(self, pos, P, k, out):
+        torch = _torch()
         if out is None:
-            out = torch.empty(self.out_shape(P, k), dtype=torch.float32, device=pos.device)
-        elif not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
-                  and out.numel() == P * ROWS[k] * self.N):
+            return torch.empty(self.out_shape(P, k), dtype=torch.float32, device=pos.device)
+        if not (out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+                and out.numel() == P * ROWS[k] * self.N):
             raise ValueError("out must be a contiguous float32 CUDA tensor of the output shape")
-        _check(load().spo_eval(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
-                               ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "spo_eval")
         return out
+
+    def eval(self, pos, kind="vgh", out=None, stream=None, algo="auto"):
+        """Evaluate at device positions pos [P, 3] (FP32 torch CUDA tensor).
+        Returns out (allocated if None): [P, N], [P, 5, N] or [P, 10, N].
+        algo: "auto", "gather", "sorted_gather" or "brick" (same values)."""
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        P = self._check_pos(pos)
+        out = self._out_for(pos, P, k, out)
+        _check(load().spo_eval_ex(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream), a),
+               "spo_eval_ex")
+        return out
+
+    def bin(self, pos, stream=None):
+        """Sort pos by brick into this set's scratch for the stream."""
+        P = self._check_pos(pos)
+        _check(load().spo_bin(self.handle, ctypes.c_void_p(pos.data_ptr()), P,
+                              _stream_handle(stream)), "spo_bin")
+
+    def eval_binned(self, pos, kind="vgh", out=None, stream=None, algo="brick"):
+        """Evaluate from the binning of the last bin(pos) on the stream."""
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        P = self._check_pos(pos)
+        out = self._out_for(pos, P, k, out)
+        _check(load().spo_eval_binned(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
+                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream), a),
+               "spo_eval_binned")
+        return out
+
+    def reserve(self, P: int, stream=None):
+        """Pre-allocate binning scratch for batches of up to P positions."""
+        _check(load().spo_reserve(self.handle, int(P), _stream_handle(stream)), "spo_reserve")
 
     def eval_v(self, pos, out=None, stream=None):
         return self.eval(pos, "v", out, stream)

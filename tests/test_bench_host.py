@@ -21,16 +21,17 @@ def test_algorithmic_bytes_per_eval():
 
 def test_traffic_record_is_dropped_when_kernel_changes(tmp_path, monkeypatch):
     rec = {"kernel_source_sha256_16": bench.kernel_source_digest(),
-           "entries": [{"workload": "w", "storage": "f32", "kind": "vgh",
+           "entries": [{"workload": "w", "storage": "f32", "kind": "vgh", "algo": "brick",
                         "dram_bytes_per_launch": 123}]}
     path = tmp_path / "t.json"
     path.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
-    assert bench.recorded_traffic("w", "f32", "vgh") == 123
-    assert bench.recorded_traffic("w", "bf16", "vgh") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "brick") == 123
+    assert bench.recorded_traffic("w", "bf16", "vgh", "brick") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "gather") is None
     rec["kernel_source_sha256_16"] = "0" * 16
     path.write_text(json.dumps(rec))
-    assert bench.recorded_traffic("w", "f32", "vgh") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "brick") is None
 
 
 def test_shard_seeds_differ_per_rank():

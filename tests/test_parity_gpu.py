@@ -22,20 +22,33 @@ def torch():
     return t
 
 
-def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None):
+ALGOS = ["gather", "sorted_gather", "brick"]
+
+
+def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None, algos=("auto",)):
+    """Outputs of every requested strategy; all must be bit-identical."""
     t = torch()
+    res = {}
     with spo.OrbitalSet(coefs_upload, storage=storage, src_dtype=src_dtype) as s:
         p = t.from_numpy(np.ascontiguousarray(pos, dtype=np.float32)).cuda()
-        o = s.eval(p, kind, out=out)
-        t.cuda.synchronize()
-        return o.cpu().numpy()
+        for a in algos:
+            if a == "brick" and s.info()["Np"] < 64:
+                continue
+            o = s.eval(p, kind, out=out, algo=a)
+            t.cuda.synchronize()
+            res[a] = o.cpu().numpy()
+        assert spo.device_status() == 0
+    first = next(iter(res.values()))
+    for a, o in res.items():
+        assert np.array_equal(o, first, equal_nan=True), f"strategy {a} differs from {next(iter(res))}"
+    return first
 
 
-def check_case(spo, coefs64, pos, kind, storage, sample=None, what=""):
+def check_case(spo, coefs64, pos, kind, storage, sample=None, what="", algos=("auto",)):
     """Kernel parity (and the format error for reduced precision)."""
     k = KINDS[kind]
     vals, upload, sd = stored_values(coefs64, storage)
-    got = gpu_eval(spo, upload, pos, kind, storage, sd)
+    got = gpu_eval(spo, upload, pos, kind, storage, sd, algos=algos)
     idx = np.arange(len(pos)) if sample is None else sample
     pos64 = np.asarray(pos, dtype=np.float64)[idx]
     ref = oracle.spo_eval(vals, pos64, k)
@@ -56,14 +69,16 @@ def check_case(spo, coefs64, pos, kind, storage, sample=None, what=""):
 def test_uniform16_vgh(spo_lib, oracle_lib):
     cfg = inputs.UNIFORM16
     c = cfg.make_coefs()
-    check_case(spo_lib, c, cfg.make_positions(), "vgh", "f32", what=cfg.name)
+    check_case(spo_lib, c, cfg.make_positions(), "vgh", "f32", what=cfg.name,
+               algos=("auto", "gather", "sorted_gather"))
 
 
 @pytest.mark.parametrize("kind", ["vgl", "vgh", "v"])
 def test_nio32_full(spo_lib, oracle_lib, kind):
     cfg = inputs.NIO32
     c = cfg.make_coefs()
-    check_case(spo_lib, c, cfg.make_positions(), kind, "f32", what=f"{cfg.name} {kind}")
+    check_case(spo_lib, c, cfg.make_positions(), kind, "f32", what=f"{cfg.name} {kind}",
+               algos=["auto"] + ALGOS)
 
 
 @pytest.fixture(scope="module")
@@ -78,54 +93,93 @@ def test_nio64_full_batch_sampled(spo_lib, oracle_lib, nio64, storage):
     checks a seeded sample of 2048 of them element by element."""
     cfg, c, pos = nio64
     sample = np.sort(np.unique((inputs.uniform01(99, 2048) * len(pos)).astype(np.int64)))
-    check_case(spo_lib, c, pos, "vgh", storage, sample=sample, what=f"{cfg.name} {storage}")
+    check_case(spo_lib, c, pos, "vgh", storage, sample=sample, what=f"{cfg.name} {storage}",
+               algos=["auto"] + ALGOS)
 
 
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("grid,N", [((4, 4, 4), 1), ((5, 9, 7), 13), ((4, 6, 5), 7),
-                                    ((8, 8, 8), 33), ((7, 4, 11), 4), ((6, 6, 6), 1024)])
+                                    ((8, 8, 8), 33), ((7, 4, 11), 4), ((6, 6, 6), 1024),
+                                    ((9, 10, 11), 100), ((4, 5, 6), 65), ((13, 6, 9), 64)])
 @pytest.mark.parametrize("kind", ["v", "vgl", "vgh"])
 def test_ragged_shapes(spo_lib, oracle_lib, grid, N, kind):
+    """Grids that are not multiples of the brick edge (partial bricks at the
+    far faces), N that is not a multiple of the tile (partial last tile, odd
+    N: scalar stores), every strategy."""
     c = inputs.uniform_coefs(*grid, N, seed=grid[0] * 100 + N)
-    pos = np.concatenate([inputs.uniform_positions(301, 5), inputs.wide_positions(200, 6)])
-    check_case(spo_lib, c, pos, kind, "f32", what=f"{grid} N={N} {kind}")
+    pos = np.concatenate([inputs.uniform_positions(1301, 5), inputs.wide_positions(1200, 6)])
+    check_case(spo_lib, c, pos, kind, "f32", what=f"{grid} N={N} {kind}", algos=["auto"] + ALGOS)
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_ragged_reduced_precision(spo_lib, oracle_lib, storage):
-    c = inputs.plane_wave_coefs(9, 10, 11, 21, seed=3)
-    pos = inputs.wide_positions(257, 8)
-    check_case(spo_lib, c, pos, "vgh", storage, what=f"ragged {storage}")
+@pytest.mark.parametrize("N", [21, 130])
+def test_ragged_reduced_precision(spo_lib, oracle_lib, storage, N):
+    c = inputs.plane_wave_coefs(9, 10, 11, N, seed=3)
+    pos = inputs.wide_positions(2057, 8)
+    check_case(spo_lib, c, pos, "vgh", storage, what=f"ragged {storage}", algos=["auto"] + ALGOS)
+
+
+def test_degenerate_position_clouds(spo_lib, oracle_lib):
+    """All positions in one cell (one brick holds every position), all at one
+    point, and a single position: every strategy."""
+    c = inputs.plane_wave_coefs(16, 12, 20, 96, seed=17)
+    rng = np.random.default_rng(3)
+    one_cell = (np.array([5, 7, 9]) + rng.uniform(0, 1, size=(3000, 3))) / np.array([16, 12, 20])
+    same = np.tile(np.array([[0.3, 0.6, 0.9]]), (1500, 1))
+    for pos, what in ((one_cell, "one cell"), (same, "one point"), (same[:1], "one position")):
+        check_case(spo_lib, c, pos.astype(np.float32), "vgh", "f32", what=what,
+                   algos=["auto"] + ALGOS)
+
+
+def test_binning_reused_for_several_kinds(spo_lib):
+    """spo_bin once, then V, VGL and VGH from the same binning (the ratio and
+    derivative evaluations of one move) equal the one-call results."""
+    t = torch()
+    c = inputs.plane_wave_coefs(20, 20, 20, 128, seed=19).astype(np.float32)
+    pos = t.from_numpy(inputs.uniform_positions(20000, 20)).cuda()
+    with spo_lib.OrbitalSet(c) as s:
+        s.bin(pos)
+        staged = {k: s.eval_binned(pos, k, algo=a) for k, a in
+                  (("v", "brick"), ("vgl", "sorted_gather"), ("vgh", "brick"))}
+        direct = {k: s.eval(pos, k, algo="gather") for k in staged}
+        t.cuda.synchronize()
+        for k in staged:
+            assert t.equal(staged[k], direct[k]), k
+        other = t.from_numpy(inputs.uniform_positions(20000, 21)).cuda()
+        with pytest.raises(spo_lib.SpoError, match="differ from the last spo_bin"):
+            s.eval_binned(other, "vgh")
 
 
 def test_special_positions(spo_lib, oracle_lib):
     """Grid nodes, cell faces, 1.0, negative and large coordinates."""
     grid = (8, 12, 10)
-    c = inputs.uniform_coefs(*grid, 12, seed=12)
+    c = inputs.uniform_coefs(*grid, 72, seed=12)
     g = np.array(grid, dtype=np.float64)
     nodes = np.array([[0, 0, 0], [7, 11, 9], [3, 6, 5], [8, 12, 10]]) / g
     pts = np.concatenate([nodes, [[1.0, 1.0, 1.0], [-1.0, -0.5, 2.0], [0.99999994, 0.0, 0.5],
                                   [-1e-7, 1e-7, -0.99999994], [123.25, -77.5, 1000.125]],
                           nodes - 1e-7, nodes + 1e-7]).astype(np.float32)
-    check_case(spo_lib, c, pts, "vgh", "f32", what="special positions")
+    check_case(spo_lib, c, pts, "vgh", "f32", what="special positions", algos=["auto"] + ALGOS)
 
 
-def test_nonfinite_positions_do_not_fault(spo_lib, oracle_lib):
+@pytest.mark.parametrize("algo", ["auto"] + ALGOS)
+def test_nonfinite_positions_do_not_fault(spo_lib, oracle_lib, algo):
     """NaN/Inf give unspecified values for that position only."""
     t = torch()
-    c = inputs.uniform_coefs(6, 6, 6, 8, seed=1)
-    pos = inputs.uniform_positions(64, 2)
+    c = inputs.uniform_coefs(6, 6, 6, 64, seed=1)
+    pos = inputs.uniform_positions(2048, 2)
     bad = pos.copy()
     bad[5] = [np.nan, 0.5, 0.5]
     bad[9] = [np.inf, -np.inf, 0.25]
     bad[17] = [3e38, -3e38, np.nan]
     with spo_lib.OrbitalSet(c.astype(np.float32)) as s:
-        o = s.eval(t.from_numpy(bad).cuda(), "vgh")
+        o = s.eval(t.from_numpy(bad).cuda(), "vgh", algo=algo)
         t.cuda.synchronize()
         got = o.cpu().numpy()
-    good = np.setdiff1d(np.arange(64), [5, 9, 17])
+        assert spo_lib.device_status() == 0
+    good = np.setdiff1d(np.arange(len(pos)), [5, 9, 17])
     vals = c.astype(np.float32).astype(np.float64)
     ref = oracle.spo_eval(vals, pos[good].astype(np.float64), 2)
     beta = oracle.condition(vals, pos[good].astype(np.float64), 2)
@@ -142,16 +196,17 @@ def test_empty_batch(spo_lib):
         assert h.shape == (0, 5, 3)
 
 
-def test_misaligned_output_uses_scalar_stores(spo_lib, oracle_lib):
+@pytest.mark.parametrize("algo", ["gather", "brick"])
+def test_misaligned_output_uses_scalar_stores(spo_lib, oracle_lib, algo):
     t = torch()
-    c = inputs.uniform_coefs(5, 6, 7, 16, seed=4)
-    pos = inputs.uniform_positions(100, 3)
+    c = inputs.uniform_coefs(5, 6, 7, 64, seed=4)
+    pos = inputs.uniform_positions(1100, 3)
     with spo_lib.OrbitalSet(c.astype(np.float32)) as s:
-        big = t.full((100 * 10 * 16 + 1,), float("nan"), device="cuda")
-        view = big[1:]   # 4-byte aligned, not 16-byte aligned
-        s.eval(t.from_numpy(pos).cuda(), "vgh", out=view)
+        big = t.full((1100 * 10 * 64 + 1,), float("nan"), device="cuda")
+        view = big[1:]   # 4-byte aligned, not 8- or 16-byte aligned
+        s.eval(t.from_numpy(pos).cuda(), "vgh", out=view, algo=algo)
         t.cuda.synchronize()
-        got = view.cpu().numpy().reshape(100, 10, 16)
+        got = view.cpu().numpy().reshape(1100, 10, 64)
         assert np.isnan(big[0].item())
     vals = c.astype(np.float32).astype(np.float64)
     ref = oracle.spo_eval(vals, pos, 2)
@@ -248,7 +303,8 @@ def test_library_conversion_rounds_once_to_nearest_even(spo_lib, storage):
         oa, ob, od = a.eval_vgh(pos), b.eval_vgh(pos), d.eval_vgh(pos)
         t.cuda.synchronize()
         assert t.equal(oa, ob) and t.equal(oa, od)
-        assert a.info()["Np"] == 24 and a.footprint() == 8 * 9 * 10 * 24 * (4 if storage == "f32" else 2)
+        assert a.info()["Np"] == 24
+        assert a.footprint() == 11 * 12 * 13 * 24 * (4 if storage == "f32" else 2)
 
 
 def test_footprint_and_padding(spo_lib):
@@ -256,7 +312,9 @@ def test_footprint_and_padding(spo_lib):
     with spo_lib.OrbitalSet(c, storage="bf16") as s:
         info = s.info()
         assert info["grid"] == (4, 5, 6) and info["N"] == 13 and info["Np"] == 16
-        assert s.footprint() == 4 * 5 * 6 * 16 * 2
+        assert s.footprint() == 7 * 8 * 9 * 16 * 2   # 3 ghost nodes per axis
+        with pytest.raises(spo_lib.SpoError, match="SPO_EUNSUPPORTED"):
+            s.eval(torch().zeros((2048, 3), device="cuda"), "vgh", algo="brick")
 
 
 def test_errors_are_reported_not_launched(spo_lib):
