@@ -312,6 +312,7 @@ def run_ours(args):
     rows = ROWS[kind]
     out = torch.empty((P, rows, cfg.N) if rows > 1 else (P, cfg.N), dtype=torch.float32, device=dev)
     s = spo.OrbitalSet(coefs32, storage=storage)
+    s.set_param("brick_vec", args.brick_vec)
     stream = torch.cuda.current_stream()
 
     algo = resolve_algo(args.algo, s, P)
@@ -378,7 +379,7 @@ def run_ours(args):
         "dtype": {"f32": "f32", "bf16": "bf16 storage, f32 accumulate",
                   "f16": "f16 storage, f32 accumulate"}[storage],
         "data": "synthetic (seeded plane-wave orbitals, uniform positions)",
-        "config": dict(base_config(cfg, storage, kind, P), algo=algo),
+        "config": dict(base_config(cfg, storage, kind, P), algo=algo, brick_vec=args.brick_vec),
         "roofline": roofline, "e2e": e2e,
         "gpu_launches": args.steps * (1 if algo == "gather" else 4),
         "clocks": sampler.summary(),
@@ -457,6 +458,7 @@ def main(argv=None):
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
     ap.add_argument("--algo", choices=["auto", "gather", "sorted_gather", "brick"], default="auto")
+    ap.add_argument("--brick-vec", type=int, choices=[2, 4], default=2)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")

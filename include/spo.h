@@ -86,6 +86,11 @@ typedef enum {
     SPO_ALGO_BRICK = 3           /* binned; each brick's table block staged in shared memory */
 } spo_algo;
 
+/* Tuning parameters of a set (see spo_set_param). */
+typedef enum {
+    SPO_PARAM_BRICK_VEC = 0   /* orbitals per thread in the brick kernel: 2 (default) or 4 */
+} spo_param;
+
 /* Opaque orbital set: one converted coefficient table resident on one GPU. */
 typedef struct spo_set spo_set;
 
@@ -196,6 +201,12 @@ spo_status spo_device_status(unsigned int *flags, int clear, void *stream);
  */
 spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
                          float *out_host, void *stream);
+
+/* Set or read a tuning parameter.  Tuning changes speed only: every value
+ * gives bit-identical outputs.  Invalid parameters or values: SPO_EINVAL.
+ * Not thread-safe against evaluations of the same set in flight on the host. */
+spo_status spo_set_param(spo_set *set, spo_param param, int64_t value);
+spo_status spo_get_param(const spo_set *set, spo_param param, int64_t *value);
 
 /* Device bytes held by the set's table (scratch and the staging buffers of
  * spo_eval_host excluded). */

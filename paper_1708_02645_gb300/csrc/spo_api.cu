@@ -535,6 +535,28 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
     return status;
 }
 
+spo_status spo_set_param(spo_set *set, spo_param param, int64_t value) {
+    g_last_error[0] = '\0';
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    switch (param) {
+        case SPO_PARAM_BRICK_VEC:
+            if (value != 2 && value != 4)
+                return fail(SPO_EINVAL, "SPO_PARAM_BRICK_VEC must be 2 or 4, not %lld", (long long)value);
+            set->brick_vec = (int)value;
+            return SPO_OK;
+    }
+    return fail(SPO_EINVAL, "unknown parameter %d", (int)param);
+}
+
+spo_status spo_get_param(const spo_set *set, spo_param param, int64_t *value) {
+    g_last_error[0] = '\0';
+    if (!set || !value) return fail(SPO_EINVAL, "set or value is NULL");
+    switch (param) {
+        case SPO_PARAM_BRICK_VEC: *value = set->brick_vec; return SPO_OK;
+    }
+    return fail(SPO_EINVAL, "unknown parameter %d", (int)param);
+}
+
 spo_status spo_footprint(const spo_set *set, size_t *bytes) {
     if (!set || !bytes) return fail(SPO_EINVAL, "set or bytes is NULL");
     *bytes = set->table_bytes;

@@ -17,16 +17,16 @@ namespace {
 using namespace spo_dev;
 using spo_detail::kBrick;
 
-__global__ void bin_count_kernel(const float *__restrict__ pos, int64_t P, int nx, int ny, int nz,
-                                 int nby, int nbz, int *__restrict__ counts, int *__restrict__ keys,
-                                 int *__restrict__ slots) {
+__global__ void bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis gy,
+                                 GridAxis gz, int nby, int nbz, int *__restrict__ counts,
+                                 int *__restrict__ keys, int *__restrict__ slots) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         int cx, cy, cz;
         float t;
-        reduce_axis(__ldg(pos + 3 * p + 0), nx, cx, t);
-        reduce_axis(__ldg(pos + 3 * p + 1), ny, cy, t);
-        reduce_axis(__ldg(pos + 3 * p + 2), nz, cz, t);
+        reduce_axis(__ldg(pos + 3 * p + 0), gx, cx, t);
+        reduce_axis(__ldg(pos + 3 * p + 1), gy, cy, t);
+        reduce_axis(__ldg(pos + 3 * p + 2), gz, cz, t);
         const int key = ((cx / kBrick) * nby + cy / kBrick) * nbz + cz / kBrick;
         keys[p] = key;
         slots[p] = atomicAdd(counts + key, 1);
@@ -107,7 +107,8 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     if (e != cudaSuccess) return e;
     const int threads = 256;
     const int blocks = (int)std::min<int64_t>((P + threads - 1) / threads, 152 * 16);
-    bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, nx, ny, nz, nby, nbz, w.counts, w.keys,
+    bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, grid_axis(nx), grid_axis(ny),
+                                                     grid_axis(nz), nby, nbz, w.counts, w.keys,
                                                      w.slots);
     bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(w.counts, w.offsets, nbins);
     bin_scatter_kernel<<<blocks, threads, 0, stream>>>(w.keys, w.slots, w.offsets, w.perm, P);

@@ -35,7 +35,6 @@ using spo_detail::kBlockEdge;
 using spo_detail::kBrick;
 
 constexpr int kThreads = 256;
-constexpr int kVec = 2;   // orbitals per thread
 constexpr int kBlockRows = kBlockEdge * kBlockEdge * kBlockEdge;   // 343
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
@@ -88,14 +87,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-template <typename T, int KIND, int TILE, bool VEC_OUT>
+template <typename T, int KIND, int TILE, int V, bool VEC_OUT>
 __global__ void __launch_bounds__(kThreads, 2)
-spo_brick_kernel(const __grid_constant__ CUtensorMap map, int nx, int ny, int nz, int nby, int nbz,
-                 int ntiles, int64_t N, const float *__restrict__ pos,
+spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
+                 int nby, int nbz, int ntiles, int64_t N, const float *__restrict__ pos,
                  const int *__restrict__ offsets, const int *__restrict__ perm,
                  float *__restrict__ out)
 {
     constexpr int NC = Rows<KIND>::value;
+    constexpr int kVec = V;                   // orbitals per thread
     constexpr int TPP = TILE / kVec;          // threads per position
     constexpr int PPR = kThreads / TPP;       // positions per round
     constexpr uint32_t kBytes = kBlockRows * TILE * sizeof(T);
@@ -127,9 +127,9 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, int nx, int ny, int nz
     for (int i = begin + threadIdx.x / TPP; i < end; i += PPR) {
         const int p = __ldg(perm + i);
         Axis X, Y, Z;
-        make_axis(__ldg(pos + 3 * p + 0), nx, X);
-        make_axis(__ldg(pos + 3 * p + 1), ny, Y);
-        make_axis(__ldg(pos + 3 * p + 2), nz, Z);
+        make_axis(__ldg(pos + 3 * p + 0), gx, X);
+        make_axis(__ldg(pos + 3 * p + 1), gy, Y);
+        make_axis(__ldg(pos + 3 * p + 2), gz, Z);
         if (!ready) {   // first position's weights were computed while the copy flew
             if (!mbar_wait_bounded(bar_s, 0)) {
                 atomicOr(&g_spo_device_status, 1u);
@@ -137,14 +137,14 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, int nx, int ny, int nz
             }
             ready = true;
         }
-        const int lx = X.cell - bx * kBrick, ly = Y.cell - by * kBrick, lz = Z.cell - bz * kBrick;
+        // the binning put the cell in this brick; the clamp keeps the shared
+        // memory index in range even if it had not
+        const int lx = min(max(X.cell - bx * kBrick, 0), kBrick - 1);
+        const int ly = min(max(Y.cell - by * kBrick, 0), kBrick - 1);
+        const int lz = min(max(Z.cell - bz * kBrick, 0), kBrick - 1);
         const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
         float acc[NC][kVec];
-#pragma unroll
-        for (int c = 0; c < NC; ++c)
-#pragma unroll
-            for (int k = 0; k < kVec; ++k) acc[c][k] = 0.0f;
-        window_reduce<KIND, kVec, false>(X, Y, Z,
+        window_reduce<KIND, kVec, true>(X, Y, Z,
                             [&](int a, int b, int g, float *v) {
                                 load_coefs<T, kVec, false>(
                                     base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
@@ -162,21 +162,22 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, int nx, int ny, int nz
 // orbitals per tile: one warp (2 orbitals per thread) per position
 constexpr int kTile = 64;
 
-template <typename T, int KIND>
+template <typename T, int KIND, int V>
 cudaError_t brick_typed(const spo_set *s, const float *pos, const spo_detail::Workspace &w,
-                        int64_t P, float *out, cudaStream_t stream) {
+                        float *out, cudaStream_t stream) {
     constexpr int TILE = kTile;
     constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
-    (void)P;
     const int nbins = s->nbx * s->nby * s->nbz;
     const int ntiles = (int)((s->N + TILE - 1) / TILE);
     const int64_t blocks = (int64_t)nbins * ntiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool vec_out = (s->N % kVec == 0) && ((reinterpret_cast<uintptr_t>(out) % (4 * kVec)) == 0);
-    auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, true> : spo_brick_kernel<T, KIND, TILE, false>;
+    const bool vec_out = (s->N % V == 0) && ((reinterpret_cast<uintptr_t>(out) % (4 * V)) == 0);
+    auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true>
+                          : spo_brick_kernel<T, KIND, TILE, V, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    kernel<<<(unsigned)blocks, kThreads, kSmem, stream>>>(s->block_map, s->nx, s->ny, s->nz, s->nby,
+    kernel<<<(unsigned)blocks, kThreads, kSmem, stream>>>(s->block_map, grid_axis(s->nx),
+                                                          grid_axis(s->ny), grid_axis(s->nz), s->nby,
                                                           s->nbz, ntiles, s->N, pos, w.offsets,
                                                           w.perm, out);
     return cudaGetLastError();
@@ -184,11 +185,18 @@ cudaError_t brick_typed(const spo_set *s, const float *pos, const spo_detail::Wo
 
 template <typename T>
 cudaError_t brick_kind(spo_kind kind, const spo_set *s, const float *pos,
-                       const spo_detail::Workspace &w, int64_t P, float *out, cudaStream_t stream) {
+                       const spo_detail::Workspace &w, float *out, cudaStream_t stream) {
+    const bool v4 = s->brick_vec == 4;
     switch (kind) {
-        case SPO_KIND_V: return brick_typed<T, SPO_KIND_V>(s, pos, w, P, out, stream);
-        case SPO_KIND_VGL: return brick_typed<T, SPO_KIND_VGL>(s, pos, w, P, out, stream);
-        case SPO_KIND_VGH: return brick_typed<T, SPO_KIND_VGH>(s, pos, w, P, out, stream);
+        case SPO_KIND_V:
+            return v4 ? brick_typed<T, SPO_KIND_V, 4>(s, pos, w, out, stream)
+                      : brick_typed<T, SPO_KIND_V, 2>(s, pos, w, out, stream);
+        case SPO_KIND_VGL:
+            return v4 ? brick_typed<T, SPO_KIND_VGL, 4>(s, pos, w, out, stream)
+                      : brick_typed<T, SPO_KIND_VGL, 2>(s, pos, w, out, stream);
+        case SPO_KIND_VGH:
+            return v4 ? brick_typed<T, SPO_KIND_VGH, 4>(s, pos, w, out, stream)
+                      : brick_typed<T, SPO_KIND_VGH, 2>(s, pos, w, out, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -217,10 +225,11 @@ namespace spo_detail {
 
 cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set, const float *pos,
                          const Workspace &w, int64_t P, float *out, cudaStream_t stream) {
+    (void)P;
     switch (storage) {
-        case SPO_F32: return brick_kind<float>(kind, set, pos, w, P, out, stream);
-        case SPO_BF16: return brick_kind<__nv_bfloat16>(kind, set, pos, w, P, out, stream);
-        case SPO_F16: return brick_kind<__half>(kind, set, pos, w, P, out, stream);
+        case SPO_F32: return brick_kind<float>(kind, set, pos, w, out, stream);
+        case SPO_BF16: return brick_kind<__nv_bfloat16>(kind, set, pos, w, out, stream);
+        case SPO_F16: return brick_kind<__half>(kind, set, pos, w, out, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -71,14 +71,28 @@ __device__ __forceinline__ void load_coefs(const T *p, float *v) {
 // per-position geometry
 // ---------------------------------------------------------------------------
 
+// Per-axis constants of a grid: n intervals, n and n^2 as floats, 1/n.
+struct GridAxis {
+    int n;
+    float fn, fn2, inv;
+};
+
+inline GridAxis grid_axis(int n) {
+    return GridAxis{n, (float)n, (float)n * (float)n, 1.0f / (float)n};
+}
+
 // Cell index i in [0, n) and fraction t in [0, 1] of coordinate r on a
 // periodic axis of n intervals.  t = r*n - floor(r*n) is formed with one
 // fused multiply-add, so it is the FP32 rounding of the exact fraction.
-// NaN or Inf coordinates end in cell 0 with t = 0.
-__device__ __forceinline__ void reduce_axis(float r, int n, int &cell, float &t) {
-    const float fn = (float)n;
-    float fl = floorf(r * fn);
-    float tt = fmaf(r, fn, -fl);
+// The cell is reduced modulo n in floating point: with |floor(r n)| <= 2^22
+// the quotient q = floor(fl / n) is off by at most one, which one range
+// check corrects, and fl - q n is an exact small integer.  Coordinates
+// beyond 2^22 cells (which carry no fractional bits in FP32 anyway), NaN and
+// Inf land in an unspecified cell; the final clamp keeps every index in
+// range whatever the input.
+__device__ __forceinline__ void reduce_axis(float r, const GridAxis &g, int &cell, float &t) {
+    float fl = floorf(r * g.fn);
+    float tt = fmaf(r, g.fn, -fl);
     if (tt < 0.0f) {
         fl -= 1.0f;
         tt += 1.0f;
@@ -87,10 +101,12 @@ __device__ __forceinline__ void reduce_axis(float r, int n, int &cell, float &t)
         tt -= 1.0f;
     }
     if (!(tt >= 0.0f && tt <= 1.0f)) tt = 0.0f;
-    fl = fminf(fmaxf(fl, -1.0e9f), 1.0e9f);   // fmaxf maps NaN to the bound
-    int c = (int)fl % n;
-    if (c < 0) c += n;
-    cell = c;
+    fl = fminf(fmaxf(fl, -4194304.0f), 4194304.0f);   // |fl| <= 2^22; fmaxf maps NaN to the bound
+    const float q = floorf(fl * g.inv);
+    float c = fmaf(-q, g.fn, fl);
+    if (c < 0.0f) c += g.fn;
+    else if (c >= g.fn) c -= g.fn;
+    cell = min(max((int)c, 0), g.n - 1);
     t = tt;
 }
 
@@ -102,10 +118,10 @@ struct Axis {
     int cell;
 };
 
-__device__ __forceinline__ void make_axis(float r, int n, Axis &ax) {
+__device__ __forceinline__ void make_axis(float r, const GridAxis &g, Axis &ax) {
     float t;
-    reduce_axis(r, n, ax.cell, t);
-    const float fn = (float)n, fn2 = fn * fn;
+    reduce_axis(r, g, ax.cell, t);
+    const float fn = g.fn, fn2 = g.fn2;
     const float s = 1.0f - t, t2 = t * t, s2 = s * s;
     ax.w[0] = (1.0f / 6.0f) * s2 * s;
     ax.w[1] = fmaf(t2, fmaf(0.5f, t, -1.0f), 2.0f / 3.0f);
@@ -124,12 +140,14 @@ __device__ __forceinline__ void make_axis(float r, int n, Axis &ax) {
 // ---------------------------------------------------------------------------
 // the window reduction
 // ---------------------------------------------------------------------------
-// acc[NC][V] += the terms of x node a (weights xw, xd, xdd) of one window,
-// for V consecutive orbitals.  load(a, b, g, v) fetches the V coefficients
-// of corner (a, b, g).  The order of every FMA is fixed here, so all kernels
-// produce the same bits for the same position and orbitals.
-template <int KIND, int V, typename Load>
-__device__ __forceinline__ void window_x_node(int a, float xw, float xd, float xdd, const Axis &Y,
+// Accumulate the terms of x node A (weights xw, xd, xdd) of one window into
+// acc[NC][V], for V consecutive orbitals; node A = 0 initialises acc.
+// load(a, b, g, v) fetches the V coefficients of corner (a, b, g).  The
+// first term of every sum is a product and each later term one FMA, in a
+// fixed order, so all kernels produce the same bits for the same position
+// and orbitals.
+template <int KIND, int V, int A, typename Load>
+__device__ __forceinline__ void window_x_node(float xw, float xd, float xdd, const Axis &Y,
                                               const Axis &Z, Load &load,
                                               float (&acc)[Rows<KIND>::value][V]) {
     constexpr int NY = KIND == SPO_KIND_V ? 1 : (KIND == SPO_KIND_VGL ? 5 : 6);
@@ -139,39 +157,52 @@ __device__ __forceinline__ void window_x_node(int a, float xw, float xd, float x
     //   V:   wy*v
     float ys[NY][V];
 #pragma unroll
-    for (int j = 0; j < NY; ++j)
-#pragma unroll
-        for (int k = 0; k < V; ++k) ys[j][k] = 0.0f;
-
-#pragma unroll
     for (int b = 0; b < 4; ++b) {
         float cv[4][V];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) load(a, b, g, cv[g]);
+        for (int g = 0; g < 4; ++g) load(A, b, g, cv[g]);
 #pragma unroll
         for (int k = 0; k < V; ++k) {
             float zv = Z.w[0] * cv[0][k];
             zv = fmaf(Z.w[1], cv[1][k], zv);
             zv = fmaf(Z.w[2], cv[2][k], zv);
             zv = fmaf(Z.w[3], cv[3][k], zv);
-            ys[0][k] = fmaf(Y.w[b], zv, ys[0][k]);
+            float zd = 0.0f, zdd = 0.0f;
             if constexpr (KIND != SPO_KIND_V) {
-                float zd = Z.d[0] * cv[0][k];
+                zd = Z.d[0] * cv[0][k];
                 zd = fmaf(Z.d[1], cv[1][k], zd);
                 zd = fmaf(Z.d[2], cv[2][k], zd);
                 zd = fmaf(Z.d[3], cv[3][k], zd);
-                float zdd = Z.dd[0] * cv[0][k];
+                zdd = Z.dd[0] * cv[0][k];
                 zdd = fmaf(Z.dd[1], cv[1][k], zdd);
                 zdd = fmaf(Z.dd[2], cv[2][k], zdd);
                 zdd = fmaf(Z.dd[3], cv[3][k], zdd);
-                ys[1][k] = fmaf(Y.d[b], zv, ys[1][k]);
-                ys[2][k] = fmaf(Y.dd[b], zv, ys[2][k]);
-                ys[3][k] = fmaf(Y.w[b], zd, ys[3][k]);
-                if constexpr (KIND == SPO_KIND_VGH) {
-                    ys[4][k] = fmaf(Y.d[b], zd, ys[4][k]);
-                    ys[5][k] = fmaf(Y.w[b], zdd, ys[5][k]);
-                } else {
-                    ys[4][k] = fmaf(Y.w[b], zdd, ys[4][k]);
+            }
+            if (b == 0) {
+                ys[0][k] = Y.w[0] * zv;
+                if constexpr (KIND != SPO_KIND_V) {
+                    ys[1][k] = Y.d[0] * zv;
+                    ys[2][k] = Y.dd[0] * zv;
+                    ys[3][k] = Y.w[0] * zd;
+                    if constexpr (KIND == SPO_KIND_VGH) {
+                        ys[4][k] = Y.d[0] * zd;
+                        ys[5][k] = Y.w[0] * zdd;
+                    } else {
+                        ys[4][k] = Y.w[0] * zdd;
+                    }
+                }
+            } else {
+                ys[0][k] = fmaf(Y.w[b], zv, ys[0][k]);
+                if constexpr (KIND != SPO_KIND_V) {
+                    ys[1][k] = fmaf(Y.d[b], zv, ys[1][k]);
+                    ys[2][k] = fmaf(Y.dd[b], zv, ys[2][k]);
+                    ys[3][k] = fmaf(Y.w[b], zd, ys[3][k]);
+                    if constexpr (KIND == SPO_KIND_VGH) {
+                        ys[4][k] = fmaf(Y.d[b], zd, ys[4][k]);
+                        ys[5][k] = fmaf(Y.w[b], zdd, ys[5][k]);
+                    } else {
+                        ys[4][k] = fmaf(Y.w[b], zdd, ys[4][k]);
+                    }
                 }
             }
         }
@@ -179,53 +210,66 @@ __device__ __forceinline__ void window_x_node(int a, float xw, float xd, float x
     // x stage
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-        acc[0][k] = fmaf(xw, ys[0][k], acc[0][k]);                 // v
-        if constexpr (KIND == SPO_KIND_VGH) {
-            acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);             // gx
-            acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);             // gy
-            acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);             // gz
-            acc[4][k] = fmaf(xdd, ys[0][k], acc[4][k]);            // hxx
-            acc[5][k] = fmaf(xd, ys[1][k], acc[5][k]);             // hxy
-            acc[6][k] = fmaf(xd, ys[3][k], acc[6][k]);             // hxz
-            acc[7][k] = fmaf(xw, ys[2][k], acc[7][k]);             // hyy
-            acc[8][k] = fmaf(xw, ys[4][k], acc[8][k]);             // hyz
-            acc[9][k] = fmaf(xw, ys[5][k], acc[9][k]);             // hzz
-        } else if constexpr (KIND == SPO_KIND_VGL) {
-            acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);             // gx
-            acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);             // gy
-            acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);             // gz
-            // lap = hxx + hyy + hzz
-            float l = fmaf(xdd, ys[0][k], acc[4][k]);
-            l = fmaf(xw, ys[2][k], l);
-            acc[4][k] = fmaf(xw, ys[4][k], l);
+        if constexpr (A == 0) {
+            acc[0][k] = xw * ys[0][k];                              // v
+            if constexpr (KIND == SPO_KIND_VGH) {
+                acc[1][k] = xd * ys[0][k];                          // gx
+                acc[2][k] = xw * ys[1][k];                          // gy
+                acc[3][k] = xw * ys[3][k];                          // gz
+                acc[4][k] = xdd * ys[0][k];                         // hxx
+                acc[5][k] = xd * ys[1][k];                          // hxy
+                acc[6][k] = xd * ys[3][k];                          // hxz
+                acc[7][k] = xw * ys[2][k];                          // hyy
+                acc[8][k] = xw * ys[4][k];                          // hyz
+                acc[9][k] = xw * ys[5][k];                          // hzz
+            } else if constexpr (KIND == SPO_KIND_VGL) {
+                acc[1][k] = xd * ys[0][k];                          // gx
+                acc[2][k] = xw * ys[1][k];                          // gy
+                acc[3][k] = xw * ys[3][k];                          // gz
+                // lap = hxx + hyy + hzz
+                float l = xdd * ys[0][k];
+                l = fmaf(xw, ys[2][k], l);
+                acc[4][k] = fmaf(xw, ys[4][k], l);
+            }
+        } else {
+            acc[0][k] = fmaf(xw, ys[0][k], acc[0][k]);
+            if constexpr (KIND == SPO_KIND_VGH) {
+                acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);
+                acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);
+                acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);
+                acc[4][k] = fmaf(xdd, ys[0][k], acc[4][k]);
+                acc[5][k] = fmaf(xd, ys[1][k], acc[5][k]);
+                acc[6][k] = fmaf(xd, ys[3][k], acc[6][k]);
+                acc[7][k] = fmaf(xw, ys[2][k], acc[7][k]);
+                acc[8][k] = fmaf(xw, ys[4][k], acc[8][k]);
+                acc[9][k] = fmaf(xw, ys[5][k], acc[9][k]);
+            } else if constexpr (KIND == SPO_KIND_VGL) {
+                acc[1][k] = fmaf(xd, ys[0][k], acc[1][k]);
+                acc[2][k] = fmaf(xw, ys[1][k], acc[2][k]);
+                acc[3][k] = fmaf(xw, ys[3][k], acc[3][k]);
+                float l = fmaf(xdd, ys[0][k], acc[4][k]);
+                l = fmaf(xw, ys[2][k], l);
+                acc[4][k] = fmaf(xw, ys[4][k], l);
+            }
         }
     }
 }
 
-// acc[NC][V] += the 64-term sums of one window (x nodes a = 0..3 in order).
-// UNROLL_A unrolls the x-node loop (all 64 loads visible to the scheduler,
-// for latency hiding on global loads); otherwise the loop stays rolled and
-// the x weights rotate through registers, which keeps only one x node's 16
-// loads live (for short-latency shared loads under a register cap).
-template <int KIND, int V, bool UNROLL_A, typename Load>
+// acc[NC][V] = the 64-term sums of one window (x nodes 0..3 in order).
+// FENCE puts a compiler barrier between x nodes, so that the loads of one
+// node are not hoisted above the arithmetic of the previous one: with
+// short-latency shared-memory loads this keeps register use under the
+// launch bound; global-memory kernels leave the scheduler free.
+template <int KIND, int V, bool FENCE, typename Load>
 __device__ __forceinline__ void window_reduce(const Axis &X, const Axis &Y, const Axis &Z,
                                               Load load, float (&acc)[Rows<KIND>::value][V]) {
-    if constexpr (UNROLL_A) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-            window_x_node<KIND, V>(a, X.w[a], X.d[a], X.dd[a], Y, Z, load, acc);
-    } else {
-        float w0 = X.w[0], w1 = X.w[1], w2 = X.w[2], w3 = X.w[3];
-        float d0 = X.d[0], d1 = X.d[1], d2 = X.d[2], d3 = X.d[3];
-        float e0 = X.dd[0], e1 = X.dd[1], e2 = X.dd[2], e3 = X.dd[3];
-#pragma unroll 1
-        for (int a = 0; a < 4; ++a) {
-            window_x_node<KIND, V>(a, w0, d0, e0, Y, Z, load, acc);
-            w0 = w1; w1 = w2; w2 = w3;
-            d0 = d1; d1 = d2; d2 = d3;
-            e0 = e1; e1 = e2; e2 = e3;
-        }
-    }
+    window_x_node<KIND, V, 0>(X.w[0], X.d[0], X.dd[0], Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    window_x_node<KIND, V, 1>(X.w[1], X.d[1], X.dd[1], Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    window_x_node<KIND, V, 2>(X.w[2], X.d[2], X.dd[2], Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    window_x_node<KIND, V, 3>(X.w[3], X.d[3], X.dd[3], Y, Z, load, acc);
 }
 
 // Streaming store of the NC x V results of one thread; o points at this

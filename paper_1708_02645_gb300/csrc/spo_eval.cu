@@ -23,9 +23,9 @@ constexpr int kVec = 4;   // orbitals per thread
 
 template <typename T, int KIND, bool VEC_OUT>
 __global__ void __launch_bounds__(kThreads)
-spo_gather_kernel(const T *__restrict__ table, int nx, int ny, int nz, int yp, int zp, int64_t Np,
-                  int64_t N, const float *__restrict__ pos, const int *__restrict__ perm, int64_t P,
-                  int G, float *__restrict__ out)
+spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxis gz, int yp, int zp,
+                  int64_t Np, int64_t N, const float *__restrict__ pos, const int *__restrict__ perm,
+                  int64_t P, int G, float *__restrict__ out)
 {
     constexpr int NC = Rows<KIND>::value;
     const int64_t item = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -35,19 +35,15 @@ spo_gather_kernel(const T *__restrict__ table, int nx, int ny, int nz, int yp, i
     const int64_t p = perm ? (int64_t)__ldg(perm + i) : i;
 
     Axis X, Y, Z;
-    make_axis(__ldg(pos + 3 * p + 0), nx, X);
-    make_axis(__ldg(pos + 3 * p + 1), ny, Y);
-    make_axis(__ldg(pos + 3 * p + 2), nz, Z);
+    make_axis(__ldg(pos + 3 * p + 0), gx, X);
+    make_axis(__ldg(pos + 3 * p + 1), gy, Y);
+    make_axis(__ldg(pos + 3 * p + 2), gz, Z);
 
     // padded node of corner (a, b, g) = (cell_x + a, cell_y + b, cell_z + g)
     const T *tq = table + (((int64_t)X.cell * yp + Y.cell) * zp + Z.cell) * Np + (int64_t)q * kVec;
     const int64_t sx = (int64_t)yp * zp * Np, sy = (int64_t)zp * Np;
     float acc[NC][kVec];
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-        for (int k = 0; k < kVec; ++k) acc[c][k] = 0.0f;
-    window_reduce<KIND, kVec, true>(X, Y, Z,
+    window_reduce<KIND, kVec, false>(X, Y, Z,
                         [&](int a, int b, int g, float *v) {
                             load_coefs<T, kVec, true>(tq + a * sx + b * sy + g * Np, v);
                         },
@@ -66,10 +62,12 @@ cudaError_t gather_typed(const spo_detail::TableView &t, const float *pos, const
     const T *table = static_cast<const T *>(t.table);
     if (vec_out)
         spo_gather_kernel<T, KIND, true><<<(unsigned)blocks, kThreads, 0, stream>>>(
-            table, t.nx, t.ny, t.nz, t.yp, t.zp, t.Np, t.N, pos, perm, P, G, out);
+            table, grid_axis(t.nx), grid_axis(t.ny), grid_axis(t.nz), t.yp, t.zp, t.Np, t.N, pos,
+            perm, P, G, out);
     else
         spo_gather_kernel<T, KIND, false><<<(unsigned)blocks, kThreads, 0, stream>>>(
-            table, t.nx, t.ny, t.nz, t.yp, t.zp, t.Np, t.N, pos, perm, P, G, out);
+            table, grid_axis(t.nx), grid_axis(t.ny), grid_axis(t.nz), t.yp, t.zp, t.Np, t.N, pos,
+            perm, P, G, out);
     return cudaGetLastError();
 }
 

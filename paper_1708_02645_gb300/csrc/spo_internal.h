@@ -47,6 +47,7 @@ struct spo_set {
                              // i' holds grid node (i' - 1) mod n
     size_t table_bytes = 0;
     int tile = 0;            // orbitals per brick-kernel tile
+    int brick_vec = 2;       // orbitals per thread in the brick kernel (2 or 4)
     CUtensorMap block_map;   // 4-D TMA map of the table, box (tile, 7, 7, 7)
     bool has_block_map = false;
 

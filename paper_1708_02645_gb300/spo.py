@@ -23,6 +23,7 @@ ALGO_AUTO, ALGO_GATHER, ALGO_SORTED_GATHER, ALGO_BRICK = 0, 1, 2, 3
 ALGOS = {"auto": ALGO_AUTO, "gather": ALGO_GATHER, "sorted_gather": ALGO_SORTED_GATHER,
          "brick": ALGO_BRICK}
 ROWS = {KIND_V: 1, KIND_VGL: 5, KIND_VGH: 10}
+PARAMS = {"brick_vec": 0}
 STATUS = {0: "SPO_OK", 1: "SPO_EINVAL", 2: "SPO_ENOMEM", 3: "SPO_ECUDA", 4: "SPO_ETIMEOUT",
           5: "SPO_EUNSUPPORTED"}
 
@@ -43,6 +44,8 @@ SIGNATURES = [
     ("spo_reserve", _INT, [_P, _I64, _P]),
     ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
+    ("spo_set_param", _INT, [_P, _INT, _I64]),
+    ("spo_get_param", _INT, [_P, _INT, ctypes.POINTER(_I64)]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
     ("spo_rows", _INT, [_INT]),
@@ -173,6 +176,15 @@ class OrbitalSet:
         if self._h is None:
             raise RuntimeError("orbital set already destroyed")
         return self._h
+
+    def set_param(self, name: str, value: int):
+        """Tuning parameter ("brick_vec": 2 or 4); outputs do not change."""
+        _check(load().spo_set_param(self.handle, PARAMS[name], int(value)), "spo_set_param")
+
+    def get_param(self, name: str) -> int:
+        v = _I64()
+        _check(load().spo_get_param(self.handle, PARAMS[name], ctypes.byref(v)), "spo_get_param")
+        return int(v.value)
 
     def footprint(self) -> int:
         b = ctypes.c_size_t()

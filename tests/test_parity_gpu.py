@@ -22,7 +22,7 @@ def torch():
     return t
 
 
-ALGOS = ["gather", "sorted_gather", "brick"]
+ALGOS = ["gather", "sorted_gather", "brick", "brick4"]
 
 
 def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None, algos=("auto",)):
@@ -32,9 +32,10 @@ def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None, al
     with spo.OrbitalSet(coefs_upload, storage=storage, src_dtype=src_dtype) as s:
         p = t.from_numpy(np.ascontiguousarray(pos, dtype=np.float32)).cuda()
         for a in algos:
-            if a == "brick" and s.info()["Np"] < 64:
+            if a.startswith("brick") and s.info()["Np"] < 64:
                 continue
-            o = s.eval(p, kind, out=out, algo=a)
+            s.set_param("brick_vec", 4 if a == "brick4" else 2)
+            o = s.eval(p, kind, out=out, algo="brick" if a == "brick4" else a)
             t.cuda.synchronize()
             res[a] = o.cpu().numpy()
         assert spo.device_status() == 0
@@ -164,7 +165,7 @@ def test_special_positions(spo_lib, oracle_lib):
     check_case(spo_lib, c, pts, "vgh", "f32", what="special positions", algos=["auto"] + ALGOS)
 
 
-@pytest.mark.parametrize("algo", ["auto"] + ALGOS)
+@pytest.mark.parametrize("algo", ["auto", "gather", "sorted_gather", "brick"])
 def test_nonfinite_positions_do_not_fault(spo_lib, oracle_lib, algo):
     """NaN/Inf give unspecified values for that position only."""
     t = torch()
@@ -305,6 +306,16 @@ def test_library_conversion_rounds_once_to_nearest_even(spo_lib, storage):
         assert t.equal(oa, ob) and t.equal(oa, od)
         assert a.info()["Np"] == 24
         assert a.footprint() == 11 * 12 * 13 * 24 * (4 if storage == "f32" else 2)
+
+
+def test_tuning_parameters(spo_lib):
+    c = inputs.uniform_coefs(4, 4, 4, 64, seed=1).astype(np.float32)
+    with spo_lib.OrbitalSet(c) as s:
+        assert s.get_param("brick_vec") == 2
+        s.set_param("brick_vec", 4)
+        assert s.get_param("brick_vec") == 4
+        with pytest.raises(spo_lib.SpoError, match="must be 2 or 4"):
+            s.set_param("brick_vec", 3)
 
 
 def test_footprint_and_padding(spo_lib):
