@@ -177,6 +177,33 @@ spo_status spo_bin(const spo_set *set, const float *pos, int64_t P, void *stream
 spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
                            float *out, void *stream, spo_algo algo);
 
+/*
+ * spo_eval_noalloc — the same evaluation as spo_eval, for callers that must
+ * not have the library allocate device memory: for example an application
+ * whose own pool allocator owns the whole GPU budget, or a loop that cannot
+ * take the device-wide synchronisation cudaMalloc and cudaFree may cause
+ * while its streams are busy.  The paper has no counterpart to this call;
+ * it exists for such callers only.
+ *
+ * It never allocates: its scratch (the position binning) is a fixed array
+ * of about 3.7 MB in the library's device code, present on every device
+ * that loads the library until the process exits.  The caller passes pos
+ * and out exactly as for spo_eval.  Limits: P <= SPO_NOALLOC_MAX_POSITIONS
+ * and a grid of at most SPO_NOALLOC_MAX_BRICKS bricks of 4x4x4 cells; larger
+ * requests return SPO_EINVAL without launching anything.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with the set's device current); make that first call before any
+ * stream capture.  All calls on a device share the one array and it keeps
+ * the last call's contents (each call clears what must start at zero):
+ * calls whose GPU work overlaps, on different streams or from several host
+ * threads, race and give wrong results, so order them (one stream does).
+ */
+#define SPO_NOALLOC_MAX_POSITIONS 262144
+#define SPO_NOALLOC_MAX_BRICKS 65536
+spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
+                            float *out, void *stream);
+
 /* Allocate (or grow) the set's scratch for `stream` to hold batches of up to
  * P positions, so that later evaluations on that stream allocate nothing.
  * Synchronous. */

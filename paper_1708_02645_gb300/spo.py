@@ -42,6 +42,7 @@ SIGNATURES = [
     ("spo_bin", _INT, [_P, _P, _I64, _P]),
     ("spo_eval_binned", _INT, [_P, _INT, _P, _I64, _P, _P, _INT]),
     ("spo_reserve", _INT, [_P, _I64, _P]),
+    ("spo_eval_noalloc", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_set_param", _INT, [_P, _INT, _I64]),
@@ -247,6 +248,18 @@ class OrbitalSet:
         _check(load().spo_eval_binned(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream), a),
                "spo_eval_binned")
+        return out
+
+    def eval_noalloc(self, pos, kind="vgh", out=None, stream=None):
+        """spo_eval_noalloc: the library allocates nothing (pass `out` to
+        allocate nothing at all); scratch is a fixed per-device array, so
+        calls must not overlap on the GPU.  P <= 262,144."""
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        P = self._check_pos(pos)
+        out = self._out_for(pos, P, k, out)
+        _check(load().spo_eval_noalloc(self.handle, k, ctypes.c_void_p(pos.data_ptr()), P,
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "spo_eval_noalloc")
         return out
 
     def reserve(self, P: int, stream=None):
