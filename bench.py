@@ -87,12 +87,12 @@ def resolve_algo(name: str, s, P: int) -> str:
         nbins *= (n + 3) // 4
     if P < 1024:
         return "gather"
-    if s.info()["Np"] >= 64 and P >= nbins:
+    if s.info()["Np"] >= 32 and P >= nbins:
         return "brick"
     return "sorted_gather" if P >= 4 * nbins else "gather"
 
 
-def recorded_traffic(workload: str, storage: str, kind: str, algo: str):
+def recorded_traffic(workload: str, storage: str, kind: str, tuning: str):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     kernel source changed since the counters were taken."""
     try:
@@ -104,7 +104,7 @@ def recorded_traffic(workload: str, storage: str, kind: str, algo: str):
         return None
     for e in rec.get("entries", []):
         if (e.get("workload") == workload and e.get("storage") == storage and e.get("kind") == kind
-                and e.get("algo") == algo):
+                and e.get("tuning") == tuning):
             return e.get("dram_bytes_per_launch")
     return None
 
@@ -243,7 +243,8 @@ def oracle_throughput(coefs64, pos, kind: str, target_s: float):
     import oracle
     k = {"v": oracle.KIND_V, "vgl": oracle.KIND_VGL, "vgh": oracle.KIND_VGH}[kind]
     N = coefs64.shape[3]
-    n0 = min(len(pos), 256)
+    n0 = min(len(pos), 4096)
+    oracle.spo_eval(coefs64, pos[:64].astype(np.float64), k)   # thread pool warm-up
     t0 = time.perf_counter()
     oracle.spo_eval(coefs64, pos[:n0].astype(np.float64), k)
     per_pos = max((time.perf_counter() - t0) / n0, 1e-9)
@@ -290,8 +291,78 @@ def measure_e2e(args, s, pos_np, out, kind, evals_per_step, world, dev):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world, dev)
     e2e = {"value": world * evals_per_step / e2e_s, "unit": "evals/s",
            "h2d_bytes_per_step": int(pos_h.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 4),
-           "ms_per_step": round(e2e_s * 1e3, 4), "api": "spo_eval_host (pinned host buffers)"}
+           "ms_per_step": round(e2e_s * 1e3, 4),
+           "api": "spo_eval_host (pinned host buffers: kernels read positions from and write "
+                  "outputs to host memory over NVLink-C2C)"}
     return e2e
+
+
+FLOPS_PER_EVAL = {"v": 168, "vgl": 600, "vgh": 656}   # factored z -> y -> x sums, FMA = 2
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(num_sms: int):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flop x the maximum SM clock (the
+    clock measured under load on this machine, MEASURED_PEAKS.json)."""
+    mhz, src = 2070.0, "nominal max SM clock"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        pass
+    return num_sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, \
+        f"{num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
+
+
+def configure(s, args):
+    s.set_param("brick_vec", args.brick_vec)
+    s.set_param("brick_tile", args.brick_tile)
+    s.set_param("brick_schedule", args.brick_schedule)
+
+
+def time_steps(s, pos, out, kind, algo, steps, warmup):
+    """ms per full evaluation (binning included), CUDA events on the stream."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        s.eval(pos, kind, out=out, algo=algo)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        s.eval(pos, kind, out=out, algo=algo)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def time_kernel(s, pos, out, kind, algo, steps):
+    """ms per launch of the evaluation kernel alone (binned strategies: bin
+    once, then time only the evaluation launches)."""
+    import torch
+    if algo == "gather":
+        return time_steps(s, pos, out, kind, algo, steps, 1)
+    stream = torch.cuda.current_stream()
+    s.bin(pos)
+    s.eval_binned(pos, kind, out=out, algo=algo)
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(steps):
+        s.eval_binned(pos, kind, out=out, algo=algo)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / steps
+
+
+def max_rel_diff(a, b, kind):
+    """max |a - b| / max |b| per output group (GPU tensors)."""
+    groups = {"v": {"V": [0]}, "vgl": {"V": [0], "G": [1, 2, 3], "L": [4]},
+              "vgh": {"V": [0], "G": [1, 2, 3], "H": [4, 5, 6, 7, 8, 9]}}[kind]
+    if a.dim() == 2:
+        a, b = a[:, None, :], b[:, None, :]
+    return {g: float((a[:, c] - b[:, c]).abs().max() / b[:, c].abs().max().clamp_min(1e-30))
+            for g, c in groups.items()}
 
 
 def run_ours(args):
@@ -303,6 +374,7 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist_init("nccl")
     dev = torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
     cfg = workload_config(args.workload)
     kind, storage = args.kind, args.storage
     coefs32 = cfg.make_coefs(np.float32)
@@ -312,7 +384,7 @@ def run_ours(args):
     rows = ROWS[kind]
     out = torch.empty((P, rows, cfg.N) if rows > 1 else (P, cfg.N), dtype=torch.float32, device=dev)
     s = spo.OrbitalSet(coefs32, storage=storage)
-    s.set_param("brick_vec", args.brick_vec)
+    configure(s, args)
     stream = torch.cuda.current_stream()
 
     algo = resolve_algo(args.algo, s, P)
@@ -320,7 +392,7 @@ def run_ours(args):
         s.eval(pos, kind, out=out, algo=algo)
     torch.cuda.synchronize()
     barrier(world)
-    sampler = ClockSampler(pci_bus_string(torch.cuda.get_device_properties(dev)))
+    sampler = ClockSampler(pci_bus_string(props))
     sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -338,33 +410,33 @@ def run_ours(args):
     evals_per_step = P * cfg.N
     value = world * evals_per_step / (ms_per_step * 1e-3)
 
-    # roofline of the dominant kernel: its own launches, timed with events on
-    # the stream it runs on (binned strategies: bin once, then time only the
-    # evaluation kernel)
-    if algo == "gather":
-        kernel_ms = ms / args.steps
-        kernel_name = "spo_gather_kernel"
-    else:
-        s.bin(pos)
-        s.eval_binned(pos, kind, out=out, algo=algo)
-        torch.cuda.synchronize()
-        k0 = torch.cuda.Event(enable_timing=True)
-        k1 = torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        for _ in range(args.steps):
-            s.eval_binned(pos, kind, out=out, algo=algo)
-        k1.record(stream)
-        torch.cuda.synchronize()
-        kernel_ms = k0.elapsed_time(k1) / args.steps
-        kernel_name = "spo_brick_kernel" if algo == "brick" else "spo_gather_kernel (binned order)"
+    # roofline of the dominant kernel (its own launches, events on its stream)
+    kernel_ms = time_kernel(s, pos, out, kind, algo, args.steps)
+    kernel_name = ("spo_brick_pipe_kernel" if args.brick_schedule == 1 else "spo_brick_kernel") \
+        if algo == "brick" else ("spo_gather_kernel" if algo == "gather"
+                                 else "spo_gather_kernel (binned order)")
+    flops = FLOPS_PER_EVAL[kind] * evals_per_step
+    tf_peak, tf_src = fp32_peak_tflops(props.multi_processor_count)
+    achieved_tf = flops / (kernel_ms * 1e-3) / 1e12
     alg = algorithmic_bytes(P, cfg.N, storage, kind)
-    achieved = alg / (kernel_ms * 1e-3) / 1e9
-    peak, peak_src = measured_hbm_peak()
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": peak_src + " (hbm_gbs, burst copy)",
-                "traffic": recorded_traffic(cfg.name, storage, kind, algo),
-                "algorithmic_bytes_per_launch": alg, "kernel_ms": round(kernel_ms, 5),
-                "kernel": f"{kernel_name}<{storage},{kind}>"}
+    achieved_gbs = alg / (kernel_ms * 1e-3) / 1e9
+    hbm_peak, hbm_src = measured_hbm_peak()
+    tuning = f"{algo}/t{args.brick_tile}/v{args.brick_vec}/s{args.brick_schedule}"
+    roofline = {
+        "bound": "alu", "achieved": round(achieved_tf, 3), "peak": round(tf_peak, 2),
+        "unit": "TFLOP/s", "frac": round(achieved_tf / tf_peak, 4),
+        "peak_source": tf_src + "; FP32 FMA issue is what limits this kernel (ncu)",
+        "traffic": recorded_traffic(cfg.name, storage, kind, tuning),
+        "kernel": f"{kernel_name}<{storage},{kind}>", "kernel_ms": round(kernel_ms, 5),
+        "flops_per_launch": flops, "flops_per_eval": FLOPS_PER_EVAL[kind],
+        "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4),
+                "peak_source": hbm_src + " (hbm_gbs, burst copy)",
+                "algorithmic_bytes_per_launch": alg,
+                "note": "algorithmic bytes (64 corner coefficients + outputs per eval); the "
+                        "staged blocks are read from DRAM about 1.6 times per launch, so the "
+                        "DRAM traffic is far below them"},
+    }
     assert spo.device_status() == 0, "a bounded device-side wait gave up"
 
     # end to end through the C ABI with host buffers (pinned), copies timed
@@ -379,13 +451,17 @@ def run_ours(args):
         "dtype": {"f32": "f32", "bf16": "bf16 storage, f32 accumulate",
                   "f16": "f16 storage, f32 accumulate"}[storage],
         "data": "synthetic (seeded plane-wave orbitals, uniform positions)",
-        "config": dict(base_config(cfg, storage, kind, P), algo=algo, brick_vec=args.brick_vec),
+        "config": dict(base_config(cfg, storage, kind, P), algo=algo, brick_vec=args.brick_vec,
+                       brick_tile=args.brick_tile, brick_schedule=args.brick_schedule),
         "roofline": roofline, "e2e": e2e,
         "gpu_launches": args.steps * (1 if algo == "gather" else 4),
         "clocks": sampler.summary(),
     }
     if world > 1:
         result["config"]["parallelism"] = f"replicas x{world} (positions sharded per rank)"
+
+    if rank == 0 and world == 1 and not args.no_variants:
+        result["variants"] = measure_variants(args, cfg, coefs32, s, pos, out, kind, storage, algo)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         coefs64 = cfg.make_coefs(np.float64)
@@ -400,6 +476,43 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
+    """Reduced-precision storage on the same positions (throughput, table
+    bytes, and the GPU-side difference from the FP32-storage outputs), and
+    the NiO-32-shaped set (V, VGL, VGH)."""
+    import torch
+    from paper_1708_02645_gb300 import spo
+    res = {}
+    steps = max(5, min(args.steps, 50))
+    if storage == "f32":
+        ref = out32.clone()
+        for st in ("bf16", "f16"):
+            with spo.OrbitalSet(coefs32, storage=st) as sv:
+                configure(sv, args)
+                o = torch.empty_like(out32)
+                step_ms = time_steps(sv, pos, o, kind, algo, steps, 3)
+                k_ms = time_kernel(sv, pos, o, kind, algo, steps)
+                sv.eval(pos, kind, out=o, algo=algo)
+                torch.cuda.synchronize()
+                res[st] = {"value": pos.shape[0] * cfg.N / (step_ms * 1e-3), "unit": "evals/s",
+                           "ms_per_step": round(step_ms, 5), "kernel_ms": round(k_ms, 5),
+                           "table_bytes": sv.footprint(),
+                           "max_rel_diff_vs_f32_storage": max_rel_diff(o, ref, kind)}
+        res["f32_table_bytes"] = s32.footprint()
+    n32 = inputs.NIO32
+    c = n32.make_coefs(np.float32)
+    p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
+    with spo.OrbitalSet(c, storage="f32") as sv:
+        configure(sv, args)
+        for kd in ("v", "vgl", "vgh"):
+            o = torch.empty(sv.out_shape(n32.P, kd), dtype=torch.float32, device=pos.device)
+            a = resolve_algo(args.algo, sv, n32.P)
+            step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
+            res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
+                                       "ms_per_step": round(step_ms, 5), "algo": a}
+    return res
 
 
 def run_reference(args):
@@ -458,10 +571,14 @@ def main(argv=None):
     ap.add_argument("--storage", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
     ap.add_argument("--algo", choices=["auto", "gather", "sorted_gather", "brick"], default="auto")
-    ap.add_argument("--brick-vec", type=int, choices=[2, 4], default=2)
+    ap.add_argument("--brick-vec", type=int, choices=[2, 4], default=4)
+    ap.add_argument("--brick-tile", type=int, choices=[32, 64], default=32)
+    ap.add_argument("--brick-schedule", type=int, choices=[0, 1], default=0)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the BF16/FP16 and NiO-32-shaped sub-results")
     ap.add_argument("--positions", type=int, default=0,
                     help="evaluate this many positions instead of the workload's (profiling)")
     args = ap.parse_args(argv)

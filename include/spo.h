@@ -88,7 +88,11 @@ typedef enum {
 
 /* Tuning parameters of a set (see spo_set_param). */
 typedef enum {
-    SPO_PARAM_BRICK_VEC = 0   /* orbitals per thread in the brick kernel: 2 (default) or 4 */
+    SPO_PARAM_BRICK_VEC = 0,  /* orbitals per thread in the brick kernel: 4 (default) or 2 */
+    SPO_PARAM_BRICK_TILE = 1, /* orbitals per staged block: 32 (default) or 64 (32 when Np < 64) */
+    SPO_PARAM_BRICK_SCHEDULE = 2 /* 0: one CTA per (brick, tile) (default); 1: one persistent
+                                    CTA per SM with a pipeline of TMA-staged blocks (4 orbitals
+                                    per thread; SPO_PARAM_BRICK_VEC then has no effect) */
 } spo_param;
 
 /* Opaque orbital set: one converted coefficient table resident on one GPU. */
@@ -154,7 +158,7 @@ spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t
  * spo_destroy); SPO_ALGO_BRICK then stages each brick's 7x7x7-node block of
  * the table in shared memory with one TMA copy per orbital tile.  Every
  * strategy evaluates the same sums in the same order: outputs are
- * bit-identical across strategies.  SPO_ALGO_BRICK needs at least 64
+ * bit-identical across strategies.  SPO_ALGO_BRICK needs at least 32
  * padded orbitals and returns SPO_EUNSUPPORTED otherwise; binned strategies need P < 2^31.  Calls with the same set and
  * stream are ordered by the stream; calls on different streams use
  * different scratch areas.  A call that allocates scratch synchronises the
@@ -186,7 +190,7 @@ spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, 
  * it exists for such callers only.
  *
  * It never allocates: its scratch (the position binning) is a fixed array
- * of about 3.7 MB in the library's device code, present on every device
+ * of about 7.9 MB in the library's device code, present on every device
  * that loads the library until the process exits.  The caller passes pos
  * and out exactly as for spo_eval.  Limits: P <= SPO_NOALLOC_MAX_POSITIONS
  * and a grid of at most SPO_NOALLOC_MAX_BRICKS bricks of 4x4x4 cells; larger
@@ -217,11 +221,14 @@ spo_status spo_device_status(unsigned int *flags, int clear, void *stream);
 
 /*
  * spo_eval_host — the same evaluation with HOST buffers: pos_host [P][3] and
- * out_host ([P][rows][N]) in host memory (pinned memory gives full copy
- * speed; pageable memory works but copies synchronously).  The positions are
- * copied to the device, evaluated and copied back in chunks on two internal
- * streams, so that copies overlap the kernels; the work is ordered after the
- * work already queued on `stream`.  Synchronous: out_host is complete on
+ * out_host ([P][rows][N]) in host memory.  If both buffers are pinned and
+ * mapped (cudaHostAlloc / cudaHostRegister, or torch's pin_memory), the
+ * kernels read the positions from and write the outputs to host memory
+ * directly over the CPU-GPU link (no staging, no copy engines), ordered on
+ * `stream`.  Otherwise the positions are copied to the device, evaluated
+ * and copied back in chunks on two internal streams, so that copies overlap
+ * the kernels (pageable memory works but copies synchronously); that work is
+ * ordered after the work already queued on `stream`.  Synchronous: out_host is complete on
  * return.  Device staging buffers are owned by the set, allocated on first
  * use and reused; they are freed by spo_destroy.  Calls on the same set must
  * not run concurrently from several host threads.

@@ -87,7 +87,9 @@ void free_workspace(spo_detail::Workspace &w) {
     cudaFree(w.keys);
     cudaFree(w.slots);
     cudaFree(w.perm);
+    cudaFree(w.sorted);
     w.counts = w.offsets = w.keys = w.slots = w.perm = nullptr;
+    w.sorted = nullptr;
     w.cap_positions = w.cap_bins = 0;
 }
 
@@ -110,7 +112,8 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
             cudaMalloc(&w->offsets, sizeof(int) * (cb + 1)) != cudaSuccess ||
             cudaMalloc(&w->keys, sizeof(int) * cp) != cudaSuccess ||
             cudaMalloc(&w->slots, sizeof(int) * cp) != cudaSuccess ||
-            cudaMalloc(&w->perm, sizeof(int) * cp) != cudaSuccess) {
+            cudaMalloc(&w->perm, sizeof(int) * cp) != cudaSuccess ||
+            cudaMalloc(&w->sorted, sizeof(float4) * cp) != cudaSuccess) {
             cudaGetLastError();
             free_workspace(*w);
             return fail(SPO_ENOMEM, "cudaMalloc of binning scratch for %lld positions failed",
@@ -169,7 +172,7 @@ spo_status check_binned_algo(const spo_set *set, spo_algo algo) {
     if (algo != SPO_ALGO_SORTED_GATHER && algo != SPO_ALGO_BRICK)
         return fail(SPO_EINVAL, "invalid algo %d for a binned evaluation", (int)algo);
     if (algo == SPO_ALGO_BRICK && !set->has_block_map)
-        return fail(SPO_EUNSUPPORTED, "the brick strategy needs at least 64 padded orbitals");
+        return fail(SPO_EUNSUPPORTED, "the brick strategy needs at least 32 padded orbitals");
     return SPO_OK;
 }
 
@@ -267,9 +270,11 @@ spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dty
     if (storage != SPO_F32 && storage != SPO_BF16 && storage != SPO_F16)
         return fail(SPO_EINVAL, "invalid storage dtype %d", (int)storage);
 
-    int device = 0;
+    int device = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
     if (coefs_on_device) {
         spo_status s = check_device_pointer(coefs, device, "coefs");
         if (s != SPO_OK) return s;
@@ -278,6 +283,7 @@ spo_status spo_create(const spo_grid *grid, const void *coefs, spo_dtype src_dty
     spo_set *set = new (std::nothrow) spo_set();
     if (!set) return fail(SPO_ENOMEM, "host allocation of the set failed");
     set->device = device;
+    set->num_sms = num_sms;
     set->nx = grid->nx;
     set->ny = grid->ny;
     set->nz = grid->nz;
@@ -459,6 +465,18 @@ spo_status spo_device_status(unsigned int *flags, int clear, void *stream) {
     return (*flags & 1u) ? fail(SPO_ETIMEOUT, "a bounded wait on a TMA copy gave up") : SPO_OK;
 }
 
+// Device address of pinned, mapped host memory, or nullptr for any other
+// kind of pointer (pageable host memory, device memory).
+const void *mapped_host_alias(const void *p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (attr.type != cudaMemoryTypeHost || !attr.devicePointer) return nullptr;
+    return attr.devicePointer;
+}
+
 spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
                          float *out_host, void *stream) {
     g_last_error[0] = '\0';
@@ -466,6 +484,20 @@ spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int
     if (s != SPO_OK || P == 0) return s;
     DeviceGuard guard(set->device);
     if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+
+    // Zero-copy: with both buffers pinned and mapped, the kernels read the
+    // positions from and write the outputs to host memory directly (over the
+    // coherent CPU-GPU link on Grace-Blackwell), with no staging copies.
+    const float *pos_dev = static_cast<const float *>(mapped_host_alias(pos_host));
+    float *out_dev = static_cast<float *>(const_cast<void *>(mapped_host_alias(out_host)));
+    if (pos_dev && out_dev && (reinterpret_cast<uintptr_t>(out_dev) & 3) == 0 &&
+        (reinterpret_cast<uintptr_t>(pos_dev) & 3) == 0) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        spo_status status = eval_queue(set, kind, pos_dev, P, out_dev, st, SPO_ALGO_AUTO);
+        if (status != SPO_OK) return status;
+        cudaError_t e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? SPO_OK : cuda_fail(e, "zero-copy evaluation");
+    }
 
     const int64_t rows = spo_rows(kind);
     const size_t out_row = (size_t)rows * (size_t)set->N * sizeof(float);   // per position
@@ -544,6 +576,16 @@ spo_status spo_set_param(spo_set *set, spo_param param, int64_t value) {
                 return fail(SPO_EINVAL, "SPO_PARAM_BRICK_VEC must be 2 or 4, not %lld", (long long)value);
             set->brick_vec = (int)value;
             return SPO_OK;
+        case SPO_PARAM_BRICK_TILE:
+            if (value != 32 && value != 64)
+                return fail(SPO_EINVAL, "SPO_PARAM_BRICK_TILE must be 32 or 64, not %lld", (long long)value);
+            set->brick_tile = (int)value;
+            return SPO_OK;
+        case SPO_PARAM_BRICK_SCHEDULE:
+            if (value != 0 && value != 1)
+                return fail(SPO_EINVAL, "SPO_PARAM_BRICK_SCHEDULE must be 0 or 1, not %lld", (long long)value);
+            set->brick_schedule = (int)value;
+            return SPO_OK;
     }
     return fail(SPO_EINVAL, "unknown parameter %d", (int)param);
 }
@@ -553,6 +595,8 @@ spo_status spo_get_param(const spo_set *set, spo_param param, int64_t *value) {
     if (!set || !value) return fail(SPO_EINVAL, "set or value is NULL");
     switch (param) {
         case SPO_PARAM_BRICK_VEC: *value = set->brick_vec; return SPO_OK;
+        case SPO_PARAM_BRICK_TILE: *value = set->brick_tile; return SPO_OK;
+        case SPO_PARAM_BRICK_SCHEDULE: *value = set->brick_schedule; return SPO_OK;
     }
     return fail(SPO_EINVAL, "unknown parameter %d", (int)param);
 }

@@ -5,7 +5,8 @@
 //   1. bin_count_kernel:  key = brick of the position's cell; slot = rank of
 //                         the position within its brick (atomic counter)
 //   2. bin_scan_kernel:   offsets = exclusive prefix sum of the counts
-//   3. bin_scatter_kernel: perm[offsets[key] + slot] = position index
+//   3. bin_scatter_kernel: perm[offsets[key] + slot] = position index, and
+//                         the position with its index in the same sorted slot
 //
 // The order inside a brick depends on atomic arrival order; every output of
 // a position depends only on that position, so results are unaffected.
@@ -89,11 +90,16 @@ bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int n
     if (tid == 0) offsets[n] = carry_s;
 }
 
-__global__ void bin_scatter_kernel(const int *__restrict__ keys, const int *__restrict__ slots,
-                                   const int *__restrict__ offsets, int *__restrict__ perm, int64_t P) {
+__global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
+                                   const int *__restrict__ slots, const int *__restrict__ offsets,
+                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
-         p += (int64_t)gridDim.x * blockDim.x)
-        perm[offsets[keys[p]] + slots[p]] = (int)p;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = offsets[keys[p]] + slots[p];
+        perm[i] = (int)p;
+        sorted[i] = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
+                                __int_as_float((int)p));
+    }
 }
 
 }  // namespace
@@ -111,7 +117,8 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
                                                      grid_axis(nz), nby, nbz, w.counts, w.keys,
                                                      w.slots);
     bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(w.counts, w.offsets, nbins);
-    bin_scatter_kernel<<<blocks, threads, 0, stream>>>(w.keys, w.slots, w.offsets, w.perm, P);
+    bin_scatter_kernel<<<blocks, threads, 0, stream>>>(pos, w.keys, w.slots, w.offsets, w.perm,
+                                                       w.sorted, P);
     return cudaGetLastError();
 }
 

@@ -1,21 +1,24 @@
-// Brick kernel: one CTA per (brick, orbital tile).
+// Brick kernel: one CTA per (brick, orbital tile of 32 or 64 orbitals).
 //
 // Positions are binned by brick (kBrick^3 cells, spo_bin.cu).  Every window
 // of a position in brick (bx, by, bz) lies in the padded table nodes
 // [4bx, 4bx+7) x [4by, 4by+7) x [4bz, 4bz+7), so one TMA copy (a 4-D box of
-// 64 orbitals x 7 x 7 x 7 nodes, 88 KB in FP32) stages everything the
+// tile x 7 x 7 x 7 nodes, 88 KB for 64 FP32 orbitals) stages everything the
 // brick's positions need for one orbital tile.  The positions of the brick
-// are then evaluated from shared memory by one warp per position (2 orbitals
-// per thread, so a corner row is one 8-byte (FP32) or 4-byte (BF16/FP16)
-// conflict-free shared load per thread); the z -> y -> x reduction and
+// are then evaluated from shared memory (2 or 4 orbitals per thread, so a
+// corner row is one conflict-free 8- or 16-byte shared load per thread for
+// FP32, 4 or 8 bytes for BF16/FP16); positions are read as sorted
+// (x, y, z, index) records written by the binning, one round ahead; the
+// z -> y -> x reduction and
 // its FMA order are those of the gather kernel (spo_device.cuh), and outputs
 // are scattered back to each position's own rows with streaming stores.
 //
 // Against the gather kernel, the table bytes moved from L2 to the SMs drop
 // from 64 rows per evaluation to 343 rows per (brick, tile), and the L2 sees
 // neighbouring bricks' blocks in launch order, so DRAM reads approach one
-// pass over the table per batch.  Two CTAs fit per SM, so one CTA's copy
-// overlaps the other's arithmetic.
+// pass over the table per batch.  Two (64-orbital tiles) or four
+// (32-orbital tiles) CTAs run per SM, so one CTA's copy overlaps the
+// others' arithmetic.
 //
 // The wait on the copy is bounded (2 s of %globaltimer): if it ever gives up,
 // the CTA sets bit 0 of the device status word and returns.
@@ -25,6 +28,7 @@
 
 #include "spo_device.cuh"
 #include "spo_internal.h"
+#include "spo_tma.cuh"
 
 __device__ unsigned int g_spo_device_status = 0;
 
@@ -34,67 +38,25 @@ using namespace spo_dev;
 using spo_detail::kBlockEdge;
 using spo_detail::kBrick;
 
-constexpr int kThreads = 256;
 constexpr int kBlockRows = kBlockEdge * kBlockEdge * kBlockEdge;   // 343
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ unsigned long long global_timer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for phase `parity` of the barrier for at most kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_timer_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_timer_ns() - t0 > kWaitLimitNs) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int c0, int c1, int c2, int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-        : "memory");
-}
+// Threads per CTA and CTAs per SM for an orbital tile: a 64-orbital FP32
+// block is 88 KB (2 CTAs of 256 threads per SM), a 32-orbital one 44 KB
+// (4 CTAs of 128 threads); either way 16 warps and at most 128 registers per
+// thread.
+template <int TILE>
+struct BrickShape {
+    static constexpr int threads = TILE >= 64 ? 256 : 128;
+    static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
+};
 
 template <typename T, int KIND, int TILE, int V, bool VEC_OUT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(BrickShape<TILE>::threads, BrickShape<TILE>::ctas_per_sm)
 spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
-                 int nby, int nbz, int ntiles, int64_t N, const float *__restrict__ pos,
-                 const int *__restrict__ offsets, const int *__restrict__ perm,
-                 float *__restrict__ out)
+                 int nby, int nbz, int ntiles, int64_t N, const int *__restrict__ offsets,
+                 const float4 *__restrict__ sorted, float *__restrict__ out, int eager)
 {
     constexpr int NC = Rows<KIND>::value;
+    constexpr int kThreads = BrickShape<TILE>::threads;
     constexpr int kVec = V;                   // orbitals per thread
     constexpr int TPP = TILE / kVec;          // threads per position
     constexpr int PPR = kThreads / TPP;       // positions per round
@@ -105,32 +67,50 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
 
     const int brick = blockIdx.x / ntiles;
     const int tile = blockIdx.x - brick * ntiles;
-    const int begin = __ldg(offsets + brick), end = __ldg(offsets + brick + 1);
-    if (begin == end) return;
     const int bz = brick % nbz, by = (brick / nbz) % nby, bx = brick / (nbz * nby);
-
     const uint32_t bar_s = smem_addr(bar);
+
+    // With `eager` (bricks hold several positions on average) the copy is
+    // issued first and the brick's position range is read while it flies;
+    // otherwise empty bricks are skipped before any copy.
+    int begin = 0, end = 0;
+    if (!eager) {
+        begin = __ldg(offsets + brick);
+        end = __ldg(offsets + brick + 1);
+        if (begin == end) return;
+    }
     if (threadIdx.x == 0) {
         mbar_init(bar_s, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
         mbar_arrive_expect_tx(bar_s, kBytes);
         tma_load_4d(smem_addr(block), &map, bar_s, tile * TILE, bz * kBrick, by * kBrick, bx * kBrick);
+    }
+    if (eager) {
+        begin = __ldg(offsets + brick);
+        end = __ldg(offsets + brick + 1);
+    }
+    __syncthreads();   // the barrier's initialisation is visible to every thread
+    if (begin == end) {   // (eager only) nothing to do, but the copy must land first
+        if (threadIdx.x == 0 && !mbar_wait_bounded(bar_s, 0)) atomicOr(&g_spo_device_status, 1u);
+        return;
     }
 
     const int q = threadIdx.x % TPP;
     const int64_t o0 = (int64_t)tile * TILE + q * kVec;   // first orbital of this thread
+    int i = begin + threadIdx.x / TPP;
+    // each round's position record (x, y, z, index) was loaded one round early
+    float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     bool ready = false;
-    for (int i = begin + threadIdx.x / TPP; i < end; i += PPR) {
-        const int p = __ldg(perm + i);
-        Axis X, Y, Z;
-        make_axis(__ldg(pos + 3 * p + 0), gx, X);
-        make_axis(__ldg(pos + 3 * p + 1), gy, Y);
-        make_axis(__ldg(pos + 3 * p + 2), gz, Z);
-        if (!ready) {   // first position's weights were computed while the copy flew
+    for (; i < end; i += PPR) {
+        const float4 nxt = i + PPR < end ? __ldg(sorted + i + PPR) : cur;
+        const int p = __float_as_int(cur.w);
+        XAxis X;
+        Axis Y, Z;
+        make_xaxis(cur.x, gx, X);
+        make_axis(cur.y, gy, Y);
+        make_axis(cur.z, gz, Z);
+        if (!ready) {   // the first position's weights were computed while the copy flew
             if (!mbar_wait_bounded(bar_s, 0)) {
                 atomicOr(&g_spo_device_status, 1u);
                 return;
@@ -144,13 +124,14 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
         const int lz = min(max(Z.cell - bz * kBrick, 0), kBrick - 1);
         const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
         float acc[NC][kVec];
-        window_reduce<KIND, kVec, true>(X, Y, Z,
+        window_reduce<KIND, kVec, true>(X, gx, Y, Z,
                             [&](int a, int b, int g, float *v) {
                                 load_coefs<T, kVec, false>(
                                     base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
                             },
                             acc);
         if (o0 < N) store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
+        cur = nxt;
     }
     if (!ready && threadIdx.x == 0) {
         // a thread with no position still must not leave while the copy
@@ -159,13 +140,206 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     }
 }
 
-// orbitals per tile: one warp (2 orbitals per thread) per position
-constexpr int kTile = 64;
+// ---------------------------------------------------------------------------
+// persistent, software-pipelined brick kernel
+// ---------------------------------------------------------------------------
+// One CTA per SM (16 warps).  CTA c owns items c, c + G, c + 2G, ... (G =
+// grid size; an item is a (brick, orbital tile) pair; empty bricks are
+// skipped), so the CTAs of the GPU sweep the table together and neighbouring
+// blocks meet in L2.  NBUF slots rotate through shared memory; filling a
+// slot means: write the item's metadata (brick, tile, first sorted position,
+// count), then one mbarrier transaction that carries the TMA copy of the
+// item's block and a bulk copy of up to kStage of its sorted position
+// records.  Consumers therefore read control data and positions from shared
+// memory only.  The slot of item k is refilled with item k + NBUF by the last
+// warp to finish with item k, so copies run NBUF - 1 items ahead.
+//
+// Work is cut into tasks of 4 positions (one per 8-lane group, 4 orbitals
+// per lane, TILE / 32 passes), items padded to whole tasks.  Warp w takes
+// tasks w, w + 16, w + 32, ... of the CTA's task stream, so a warp never
+// waits for the other warps of an item.  Every warp waits on every slot
+// fill in sequence order (this keeps barrier phases unambiguous) and
+// releases every item in order once its next task lies beyond it.  The fill
+// after the last item carries an end marker.  The fill for item m is issued
+// once every warp released item m - NBUF; the earliest item not yet released
+// by all warps always has its fill issued, so the pipeline cannot deadlock.
+// Waits are bounded (bit 0 of the device status word on time-out).
+constexpr int kStage = 128;   // position records staged per item
 
-template <typename T, int KIND, int V>
-cudaError_t brick_typed(const spo_set *s, const float *pos, const spo_detail::Workspace &w,
-                        float *out, cudaStream_t stream) {
-    constexpr int TILE = kTile;
+struct __align__(16) SlotMeta {
+    int j;        // index of the item in the CTA's sequence (-1: end marker)
+    int cnt;      // positions in the brick
+    int begin;    // first sorted position of the brick
+    int tile;     // orbital tile
+    int bx, by, bz;   // brick coordinates
+    int pad;
+};
+
+template <typename T, int TILE>
+struct PipeShape {
+    static constexpr int threads = 512;
+    static constexpr int warps = threads / 32;
+    static constexpr uint32_t block_bytes = kBlockRows * TILE * sizeof(T);
+    static constexpr uint32_t block_stride = (block_bytes + 1023u) / 1024u * 1024u;
+    static constexpr uint32_t stage_bytes = kStage * 16u;
+    static constexpr int buffers_fit = (int)((200u * 1024u) / (block_stride + stage_bytes));
+    static constexpr int nbuf = buffers_fit >= 4 ? 4 : (buffers_fit >= 3 ? 3 : 2);
+    static constexpr size_t stage_off = (size_t)nbuf * block_stride;
+    static constexpr size_t meta_off = stage_off + (size_t)nbuf * stage_bytes;
+    static constexpr size_t bar_off = meta_off + (size_t)nbuf * sizeof(SlotMeta);
+    static constexpr size_t rel_off = bar_off + 8 * (size_t)nbuf;
+    static constexpr size_t smem = rel_off + 4 * (size_t)nbuf;
+};
+
+template <typename T, int KIND, int TILE, bool VEC_OUT>
+__global__ void __launch_bounds__(512, 1)
+spo_brick_pipe_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
+                      int nby, int nbz, int ntiles, int nitems, int64_t N,
+                      const int *__restrict__ offsets, const float4 *__restrict__ sorted,
+                      float *__restrict__ out)
+{
+    using Shape = PipeShape<T, TILE>;
+    constexpr int NC = Rows<KIND>::value;
+    constexpr int NBUF = Shape::nbuf;
+    constexpr int NWARPS = Shape::warps;
+    constexpr int PASSES = TILE / 32;
+    constexpr int kVec = 4;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const float4 *stage = reinterpret_cast<const float4 *>(smem + Shape::stage_off);
+    SlotMeta *meta = reinterpret_cast<SlotMeta *>(smem + Shape::meta_off);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + Shape::bar_off);
+    int *released = reinterpret_cast<int *>(smem + Shape::rel_off);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int group = lane >> 3, gl = lane & 7;
+    const int G = gridDim.x;
+
+    // producer helpers (one thread at a time): the smallest j' >= j whose
+    // item is non-empty, or -1; and the fill of a slot
+    auto next_nonempty = [&](int j) -> int {
+        for (;; ++j) {
+            const int64_t item = (int64_t)blockIdx.x + (int64_t)j * G;
+            if (item >= nitems) return -1;
+            const int b = (int)(item / ntiles);
+            if (__ldg(offsets + b + 1) > __ldg(offsets + b)) return j;
+        }
+    };
+    auto fill = [&](int j, int slot) {
+        const uint32_t bar = smem_addr(full + slot);
+        SlotMeta &sm = meta[slot];
+        if (j < 0) {   // end marker: no copy, the arrival alone completes the phase
+            sm.j = -1;
+            sm.cnt = 0;
+            mbar_arrive(bar);
+            return;
+        }
+        const int item = blockIdx.x + j * G;
+        const int brick = item / ntiles, tile = item - brick * ntiles;
+        const int begin = __ldg(offsets + brick), cnt = __ldg(offsets + brick + 1) - begin;
+        const int bz = brick % nbz, by = (brick / nbz) % nby, bx = brick / (nbz * nby);
+        sm.j = j;
+        sm.cnt = cnt;
+        sm.begin = begin;
+        sm.tile = tile;
+        sm.bx = bx;
+        sm.by = by;
+        sm.bz = bz;
+        const int staged = min(cnt, kStage);
+        mbar_arrive_expect_tx(bar, Shape::block_bytes + 16u * (uint32_t)staged);
+        tma_load_4d(smem_addr(smem + (size_t)slot * Shape::block_stride), &map, bar, tile * TILE,
+                    bz * kBrick, by * kBrick, bx * kBrick);
+        bulk_load(smem_addr(stage + (size_t)slot * kStage), sorted + begin, 16u * (uint32_t)staged,
+                  bar);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NBUF; ++s) {
+            mbar_init(smem_addr(full + s), 1);
+            released[s] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // the first NBUF fills (end marker after the last item)
+        int j = next_nonempty(0);
+        for (int s = 0; s < NBUF; ++s) {
+            fill(j, s);
+            if (j < 0) break;
+            j = next_nonempty(j + 1);
+        }
+    }
+
+    // warp-uniform cursor: sequence number k of the current item and the
+    // task just past it (its metadata stays in the slot, read per task)
+    int k = 0, tend = 0;
+    auto enter = [&](int kk) -> bool {   // wait for item kk's fill; false at the end
+        const int slot = kk % NBUF;
+        if (!mbar_wait_bounded(smem_addr(full + slot), (kk / NBUF) & 1)) {
+            if (lane == 0) atomicOr(&g_spo_device_status, 1u);
+            return false;
+        }
+        if (meta[slot].j < 0) return false;
+        tend += (meta[slot].cnt + 3) >> 2;
+        return true;
+    };
+    if (!enter(0)) return;
+
+    for (int t = warp;; t += NWARPS) {
+        // move past items wholly before task t: release each in order; the
+        // last warp to release item k refills its slot with item k + NBUF
+        while (t >= tend) {
+            const int slot = k % NBUF;
+            __syncwarp();
+            if (lane == 0 && atomicAdd(released + slot, 1) == NWARPS - 1) {
+                int ja = meta[slot].j;
+                released[slot] = 0;
+                for (int s = 0; s < NBUF && ja >= 0; ++s) ja = next_nonempty(ja + 1);
+                fill(ja, slot);
+            }
+            __syncwarp();
+            ++k;
+            if (!enter(k)) return;
+        }
+        const int slot = k % NBUF;
+        const SlotMeta sm = meta[slot];
+        const int local = (t - (tend - ((sm.cnt + 3) >> 2))) * 4 + group;
+        if (local < sm.cnt) {
+            const float4 rec = local < kStage ? stage[slot * kStage + local]
+                                              : __ldg(sorted + sm.begin + local);
+            const int p = __float_as_int(rec.w);
+            XAxis X;
+            Axis Y, Z;
+            make_xaxis(rec.x, gx, X);
+            make_axis(rec.y, gy, Y);
+            make_axis(rec.z, gz, Z);
+            const int lx = min(max(X.cell - sm.bx * kBrick, 0), kBrick - 1);
+            const int ly = min(max(Y.cell - sm.by * kBrick, 0), kBrick - 1);
+            const int lz = min(max(Z.cell - sm.bz * kBrick, 0), kBrick - 1);
+            const T *block = reinterpret_cast<const T *>(smem + (size_t)slot * Shape::block_stride);
+            const int64_t tile0 = (int64_t)sm.tile * TILE;
+#pragma unroll 1
+            for (int pass = 0; pass < PASSES; ++pass) {
+                const int o_tile = pass * 32 + gl * kVec;   // orbital within the tile
+                const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + o_tile;
+                float acc[NC][kVec];
+                window_reduce<KIND, kVec, true>(X, gx, Y, Z,
+                                    [&](int a, int b, int g, float *v) {
+                                        load_coefs<T, kVec, false>(
+                                            base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
+                                    },
+                                    acc);
+                const int64_t o0 = tile0 + o_tile;
+                if (o0 < N)
+                    store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
+            }
+        }
+    }
+}
+
+template <typename T, int KIND, int TILE, int V>
+cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P, float *out,
+                         cudaStream_t stream) {
     constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
     const int nbins = s->nbx * s->nby * s->nbz;
     const int ntiles = (int)((s->N + TILE - 1) / TILE);
@@ -176,27 +350,56 @@ cudaError_t brick_typed(const spo_set *s, const float *pos, const spo_detail::Wo
                           : spo_brick_kernel<T, KIND, TILE, V, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
-    kernel<<<(unsigned)blocks, kThreads, kSmem, stream>>>(s->block_map, grid_axis(s->nx),
-                                                          grid_axis(s->ny), grid_axis(s->nz), s->nby,
-                                                          s->nbz, ntiles, s->N, pos, w.offsets,
-                                                          w.perm, out);
+    const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
+    const int eager = P >= 4 * (int64_t)nbins;   // about 4+ positions per brick
+    kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
+        map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
+        w.offsets, w.sorted, out, eager);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t brick_kind(spo_kind kind, const spo_set *s, const float *pos,
-                       const spo_detail::Workspace &w, float *out, cudaStream_t stream) {
+template <typename T, int KIND, int TILE>
+cudaError_t brick_pipe_launch(const spo_set *s, const spo_detail::Workspace &w, float *out,
+                              cudaStream_t stream) {
+    using Shape = PipeShape<T, TILE>;
+    const int nbins = s->nbx * s->nby * s->nbz;
+    const int ntiles = (int)((s->N + TILE - 1) / TILE);
+    const int64_t nitems = (int64_t)nbins * ntiles;
+    if (nitems > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const bool vec_out = (s->N % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) % 16) == 0);
+    auto kernel = vec_out ? spo_brick_pipe_kernel<T, KIND, TILE, true>
+                          : spo_brick_pipe_kernel<T, KIND, TILE, false>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Shape::smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(nitems, s->num_sms);
+    kernel<<<grid, Shape::threads, Shape::smem, stream>>>(
+        s->block_map[TILE == 64 ? 1 : 0], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz),
+        s->nby, s->nbz, ntiles, (int)nitems, s->N, w.offsets, w.sorted, out);
+    return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+cudaError_t brick_typed(const spo_set *s, const spo_detail::Workspace &w, int64_t P, float *out,
+                        cudaStream_t stream) {
+    if (s->brick_schedule == 1)
+        return spo_detail::brick_tile_of(s) == 64 ? brick_pipe_launch<T, KIND, 64>(s, w, out, stream)
+                                                  : brick_pipe_launch<T, KIND, 32>(s, w, out, stream);
     const bool v4 = s->brick_vec == 4;
+    if (spo_detail::brick_tile_of(s) == 64)
+        return v4 ? brick_launch<T, KIND, 64, 4>(s, w, P, out, stream)
+                  : brick_launch<T, KIND, 64, 2>(s, w, P, out, stream);
+    return v4 ? brick_launch<T, KIND, 32, 4>(s, w, P, out, stream)
+              : brick_launch<T, KIND, 32, 2>(s, w, P, out, stream);
+}
+
+template <typename T>
+cudaError_t brick_kind(spo_kind kind, const spo_set *s, const spo_detail::Workspace &w, int64_t P,
+                       float *out, cudaStream_t stream) {
     switch (kind) {
-        case SPO_KIND_V:
-            return v4 ? brick_typed<T, SPO_KIND_V, 4>(s, pos, w, out, stream)
-                      : brick_typed<T, SPO_KIND_V, 2>(s, pos, w, out, stream);
-        case SPO_KIND_VGL:
-            return v4 ? brick_typed<T, SPO_KIND_VGL, 4>(s, pos, w, out, stream)
-                      : brick_typed<T, SPO_KIND_VGL, 2>(s, pos, w, out, stream);
-        case SPO_KIND_VGH:
-            return v4 ? brick_typed<T, SPO_KIND_VGH, 4>(s, pos, w, out, stream)
-                      : brick_typed<T, SPO_KIND_VGH, 2>(s, pos, w, out, stream);
+        case SPO_KIND_V: return brick_typed<T, SPO_KIND_V>(s, w, P, out, stream);
+        case SPO_KIND_VGL: return brick_typed<T, SPO_KIND_VGL>(s, w, P, out, stream);
+        case SPO_KIND_VGH: return brick_typed<T, SPO_KIND_VGH>(s, w, P, out, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -225,20 +428,22 @@ namespace spo_detail {
 
 cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set, const float *pos,
                          const Workspace &w, int64_t P, float *out, cudaStream_t stream) {
-    (void)P;
+    (void)pos;   // the brick kernel reads the sorted copy of the positions
     switch (storage) {
-        case SPO_F32: return brick_kind<float>(kind, set, pos, w, out, stream);
-        case SPO_BF16: return brick_kind<__nv_bfloat16>(kind, set, pos, w, out, stream);
-        case SPO_F16: return brick_kind<__half>(kind, set, pos, w, out, stream);
+        case SPO_F32: return brick_kind<float>(kind, set, w, P, out, stream);
+        case SPO_BF16: return brick_kind<__nv_bfloat16>(kind, set, w, P, out, stream);
+        case SPO_F16: return brick_kind<__half>(kind, set, w, P, out, stream);
         default: return cudaErrorInvalidValue;
     }
 }
 
+int brick_tile_of(const spo_set *s) {
+    return (s->brick_tile == 64 && s->Np >= 64) ? 64 : 32;
+}
+
 spo_status make_block_map(spo_set *s) {
     s->has_block_map = false;
-    const int tile = kTile;
-    s->tile = tile;
-    if (s->Np < tile) return SPO_OK;   // too few orbitals: the gather kernel serves this set
+    if (s->Np < 32) return SPO_OK;   // too few orbitals: the gather kernels serve this set
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return fail(SPO_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const size_t es = s->storage == SPO_F32 ? 4 : 2;
@@ -249,12 +454,16 @@ spo_status make_block_map(spo_set *s) {
                                 (cuuint64_t)s->xp};
     const cuuint64_t strides[3] = {(cuuint64_t)s->Np * es, (cuuint64_t)s->zp * s->Np * es,
                                    (cuuint64_t)s->yp * s->zp * s->Np * es};
-    const cuuint32_t box[4] = {(cuuint32_t)tile, kBlockEdge, kBlockEdge, kBlockEdge};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUresult r = enc(&s->block_map, dt, 4, s->table, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(SPO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    for (int k = 0; k < 2; ++k) {   // box widths 32 and 64 orbitals
+        const cuuint32_t tile = k == 0 ? 32 : 64;
+        if (s->Np < (int64_t)tile) continue;
+        const cuuint32_t box[4] = {tile, kBlockEdge, kBlockEdge, kBlockEdge};
+        CUresult r = enc(&s->block_map[k], dt, 4, s->table, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(SPO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
     s->has_block_map = true;
     return SPO_OK;
 }

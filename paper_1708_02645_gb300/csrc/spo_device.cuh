@@ -110,9 +110,37 @@ __device__ __forceinline__ void reduce_axis(float r, const GridAxis &g, int &cel
     t = tt;
 }
 
-// Cubic B-spline weights of the four window nodes (i-1, i, i+1, i+2) at
-// fraction t, with first and second derivatives scaled to d/dr (factors n
-// and n^2).
+// Cubic B-spline weight of window node A (A = 0..3 for nodes i-1 .. i+2) at
+// fraction t, with its first and second derivatives scaled to d/dr
+// (factors n and n^2).  Every kernel computes a weight with this one
+// function, so weights (and the sums built from them) agree bit for bit.
+template <int A>
+__device__ __forceinline__ void node_weights(float t, const GridAxis &g, float &w, float &d,
+                                             float &dd) {
+    if constexpr (A == 0) {
+        const float s = 1.0f - t, s2 = s * s;
+        w = (1.0f / 6.0f) * s2 * s;
+        d = -0.5f * s2 * g.fn;
+        dd = s * g.fn2;
+    } else if constexpr (A == 1) {
+        const float t2 = t * t;
+        w = fmaf(t2, fmaf(0.5f, t, -1.0f), 2.0f / 3.0f);
+        d = fmaf(1.5f, t, -2.0f) * t * g.fn;
+        dd = fmaf(3.0f, t, -2.0f) * g.fn2;
+    } else if constexpr (A == 2) {
+        w = fmaf(fmaf(fmaf(-0.5f, t, 0.5f), t, 0.5f), t, 1.0f / 6.0f);
+        d = fmaf(fmaf(-1.5f, t, 1.0f), t, 0.5f) * g.fn;
+        dd = fmaf(-3.0f, t, 1.0f) * g.fn2;
+    } else {
+        const float t2 = t * t;
+        w = (1.0f / 6.0f) * t2 * t;
+        d = 0.5f * t2 * g.fn;
+        dd = t * g.fn2;
+    }
+}
+
+// Fraction, cell and all twelve weights of one axis (y and z, which every
+// x node of the window reuses).
 struct Axis {
     float w[4], d[4], dd[4];
     int cell;
@@ -121,20 +149,21 @@ struct Axis {
 __device__ __forceinline__ void make_axis(float r, const GridAxis &g, Axis &ax) {
     float t;
     reduce_axis(r, g, ax.cell, t);
-    const float fn = g.fn, fn2 = g.fn2;
-    const float s = 1.0f - t, t2 = t * t, s2 = s * s;
-    ax.w[0] = (1.0f / 6.0f) * s2 * s;
-    ax.w[1] = fmaf(t2, fmaf(0.5f, t, -1.0f), 2.0f / 3.0f);
-    ax.w[2] = fmaf(fmaf(fmaf(-0.5f, t, 0.5f), t, 0.5f), t, 1.0f / 6.0f);
-    ax.w[3] = (1.0f / 6.0f) * t2 * t;
-    ax.d[0] = -0.5f * s2 * fn;
-    ax.d[1] = fmaf(1.5f, t, -2.0f) * t * fn;
-    ax.d[2] = fmaf(fmaf(-1.5f, t, 1.0f), t, 0.5f) * fn;
-    ax.d[3] = 0.5f * t2 * fn;
-    ax.dd[0] = s * fn2;
-    ax.dd[1] = fmaf(3.0f, t, -2.0f) * fn2;
-    ax.dd[2] = fmaf(-3.0f, t, 1.0f) * fn2;
-    ax.dd[3] = t * fn2;
+    node_weights<0>(t, g, ax.w[0], ax.d[0], ax.dd[0]);
+    node_weights<1>(t, g, ax.w[1], ax.d[1], ax.dd[1]);
+    node_weights<2>(t, g, ax.w[2], ax.d[2], ax.dd[2]);
+    node_weights<3>(t, g, ax.w[3], ax.d[3], ax.dd[3]);
+}
+
+// Fraction and cell of the x axis: its weights are formed node by node
+// inside the window reduction (fewer live registers).
+struct XAxis {
+    float t;
+    int cell;
+};
+
+__device__ __forceinline__ void make_xaxis(float r, const GridAxis &g, XAxis &ax) {
+    reduce_axis(r, g, ax.cell, ax.t);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,15 +290,21 @@ __device__ __forceinline__ void window_x_node(float xw, float xd, float xdd, con
 // short-latency shared-memory loads this keeps register use under the
 // launch bound; global-memory kernels leave the scheduler free.
 template <int KIND, int V, bool FENCE, typename Load>
-__device__ __forceinline__ void window_reduce(const Axis &X, const Axis &Y, const Axis &Z,
-                                              Load load, float (&acc)[Rows<KIND>::value][V]) {
-    window_x_node<KIND, V, 0>(X.w[0], X.d[0], X.dd[0], Y, Z, load, acc);
+__device__ __forceinline__ void window_reduce(const XAxis &X, const GridAxis &gx, const Axis &Y,
+                                              const Axis &Z, Load load,
+                                              float (&acc)[Rows<KIND>::value][V]) {
+    float xw, xd, xdd;
+    node_weights<0>(X.t, gx, xw, xd, xdd);
+    window_x_node<KIND, V, 0>(xw, xd, xdd, Y, Z, load, acc);
     if constexpr (FENCE) asm volatile("" ::: "memory");
-    window_x_node<KIND, V, 1>(X.w[1], X.d[1], X.dd[1], Y, Z, load, acc);
+    node_weights<1>(X.t, gx, xw, xd, xdd);
+    window_x_node<KIND, V, 1>(xw, xd, xdd, Y, Z, load, acc);
     if constexpr (FENCE) asm volatile("" ::: "memory");
-    window_x_node<KIND, V, 2>(X.w[2], X.d[2], X.dd[2], Y, Z, load, acc);
+    node_weights<2>(X.t, gx, xw, xd, xdd);
+    window_x_node<KIND, V, 2>(xw, xd, xdd, Y, Z, load, acc);
     if constexpr (FENCE) asm volatile("" ::: "memory");
-    window_x_node<KIND, V, 3>(X.w[3], X.d[3], X.dd[3], Y, Z, load, acc);
+    node_weights<3>(X.t, gx, xw, xd, xdd);
+    window_x_node<KIND, V, 3>(xw, xd, xdd, Y, Z, load, acc);
 }
 
 // Streaming store of the NC x V results of one thread; o points at this

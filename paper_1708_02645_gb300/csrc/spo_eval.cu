@@ -34,8 +34,9 @@ spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxi
     const int q = (int)(item - i * G);
     const int64_t p = perm ? (int64_t)__ldg(perm + i) : i;
 
-    Axis X, Y, Z;
-    make_axis(__ldg(pos + 3 * p + 0), gx, X);
+    XAxis X;
+    Axis Y, Z;
+    make_xaxis(__ldg(pos + 3 * p + 0), gx, X);
     make_axis(__ldg(pos + 3 * p + 1), gy, Y);
     make_axis(__ldg(pos + 3 * p + 2), gz, Z);
 
@@ -43,7 +44,7 @@ spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxi
     const T *tq = table + (((int64_t)X.cell * yp + Y.cell) * zp + Z.cell) * Np + (int64_t)q * kVec;
     const int64_t sx = (int64_t)yp * zp * Np, sy = (int64_t)zp * Np;
     float acc[NC][kVec];
-    window_reduce<KIND, kVec, false>(X, Y, Z,
+    window_reduce<KIND, kVec, false>(X, gx, Y, Z,
                         [&](int a, int b, int g, float *v) {
                             load_coefs<T, kVec, true>(tq + a * sx + b * sy + g * Np, v);
                         },

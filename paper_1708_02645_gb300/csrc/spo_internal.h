@@ -19,7 +19,8 @@ constexpr int kBrick = 4;
 constexpr int kBlockEdge = kBrick + 3;
 
 // Scratch of the binned path for one stream: brick counts and offsets, one
-// key and slot per position, and the position permutation sorted by brick.
+// key and slot per position, the position permutation sorted by brick, and
+// the positions themselves in that order (x, y, z, original index as bits).
 struct Workspace {
     cudaStream_t stream = nullptr;
     int *counts = nullptr;    // [nbins]
@@ -27,6 +28,7 @@ struct Workspace {
     int *keys = nullptr;      // [P]
     int *slots = nullptr;     // [P]
     int *perm = nullptr;      // [P]
+    float4 *sorted = nullptr; // [P]
     int64_t cap_positions = 0;
     int64_t cap_bins = 0;
     const float *binned_pos = nullptr;   // positions of the last binning
@@ -46,10 +48,12 @@ struct spo_set {
     void *table = nullptr;   // [xp][yp][zp][Np] of the storage type; padded node
                              // i' holds grid node (i' - 1) mod n
     size_t table_bytes = 0;
-    int tile = 0;            // orbitals per brick-kernel tile
-    int brick_vec = 2;       // orbitals per thread in the brick kernel (2 or 4)
-    CUtensorMap block_map;   // 4-D TMA map of the table, box (tile, 7, 7, 7)
-    bool has_block_map = false;
+    int brick_vec = 4;       // orbitals per thread in the brick kernel (2 or 4)
+    int brick_tile = 32;     // orbitals per brick-kernel tile (32 or 64)
+    int brick_schedule = 0;  // 0: one CTA per (brick, tile); 1: persistent pipelined CTAs
+    int num_sms = 0;         // multiprocessors of the set's device
+    CUtensorMap block_map[2];   // 4-D TMA maps of the table, boxes (32 | 64, 7, 7, 7)
+    bool has_block_map = false; // Np >= 32: the brick kernel can serve this set
 
     // scratch of the binned path, one per stream (guarded by mu)
     std::mutex mu;
@@ -102,8 +106,11 @@ cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set,
 cudaError_t launch_convert(const void *src, spo_dtype src_dtype, int x0, int x1,
                            const spo_set *set, cudaStream_t stream);
 
-// Build the brick kernel's tensor map for a set (host; driver entry point).
+// Build the brick kernel's tensor maps for a set (host; driver entry point).
 spo_status make_block_map(spo_set *set);
+
+// Orbital tile the brick kernel uses for a set (brick_tile, limited by Np).
+int brick_tile_of(const spo_set *set);
 
 // Device-side error word (bounded waits that gave up); read and clear.
 cudaError_t read_device_status(unsigned int *flags, bool clear, cudaStream_t stream);

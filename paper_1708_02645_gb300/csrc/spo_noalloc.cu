@@ -7,7 +7,8 @@
 // the device-wide synchronisation that cudaMalloc and cudaFree may cause in
 // the middle of its stream pipeline.  This entry point serves them: it
 // allocates nothing on any call, and its scratch (brick counts and offsets,
-// one key, slot and permutation entry per position) is the array below,
+// one key, slot, permutation entry and sorted position per position) is the
+// array below (7.9 MB),
 // which exists once per device from the time the library's device code is
 // loaded on that device until the process exits.
 //
@@ -33,15 +34,16 @@ namespace {
 constexpr size_t kMaxPositions = SPO_NOALLOC_MAX_POSITIONS;
 constexpr size_t kMaxBricks = SPO_NOALLOC_MAX_BRICKS;
 
-// [counts: kMaxBricks][offsets: kMaxBricks + 1][keys][slots][perm: kMaxPositions each],
-// every part starting on a 256-byte boundary
+// [counts: kMaxBricks][offsets: kMaxBricks + 1][keys][slots][perm: kMaxPositions ints each]
+// [sorted: kMaxPositions float4], every part starting on a 256-byte boundary
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kCountsOff = 0;
 constexpr size_t kOffsetsOff = kCountsOff + align256(kMaxBricks * sizeof(int));
 constexpr size_t kKeysOff = kOffsetsOff + align256((kMaxBricks + 1) * sizeof(int));
 constexpr size_t kSlotsOff = kKeysOff + align256(kMaxPositions * sizeof(int));
 constexpr size_t kPermOff = kSlotsOff + align256(kMaxPositions * sizeof(int));
-constexpr size_t kScratchBytes = kPermOff + align256(kMaxPositions * sizeof(int));
+constexpr size_t kSortedOff = kPermOff + align256(kMaxPositions * sizeof(int));
+constexpr size_t kScratchBytes = kSortedOff + align256(kMaxPositions * sizeof(float4));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -118,6 +120,7 @@ extern "C" spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const 
         w.keys = reinterpret_cast<int *>(base + kKeysOff);
         w.slots = reinterpret_cast<int *>(base + kSlotsOff);
         w.perm = reinterpret_cast<int *>(base + kPermOff);
+        w.sorted = reinterpret_cast<float4 *>(base + kSortedOff);
         w.cap_positions = (int64_t)kMaxPositions;
         w.cap_bins = (int64_t)kMaxBricks;
         cudaError_t e = spo_detail::launch_bin(pos, P, set->nx, set->ny, set->nz, set->nbx, set->nby,

@@ -23,7 +23,7 @@ ALGO_AUTO, ALGO_GATHER, ALGO_SORTED_GATHER, ALGO_BRICK = 0, 1, 2, 3
 ALGOS = {"auto": ALGO_AUTO, "gather": ALGO_GATHER, "sorted_gather": ALGO_SORTED_GATHER,
          "brick": ALGO_BRICK}
 ROWS = {KIND_V: 1, KIND_VGL: 5, KIND_VGH: 10}
-PARAMS = {"brick_vec": 0}
+PARAMS = {"brick_vec": 0, "brick_tile": 1, "brick_schedule": 2}
 STATUS = {0: "SPO_OK", 1: "SPO_EINVAL", 2: "SPO_ENOMEM", 3: "SPO_ECUDA", 4: "SPO_ETIMEOUT",
           5: "SPO_EUNSUPPORTED"}
 
@@ -179,7 +179,8 @@ class OrbitalSet:
         return self._h
 
     def set_param(self, name: str, value: int):
-        """Tuning parameter ("brick_vec": 2 or 4); outputs do not change."""
+        """Tuning parameter ("brick_vec": 2 or 4, "brick_tile": 32 or 64,
+        "brick_schedule": 0 or 1); outputs do not change."""
         _check(load().spo_set_param(self.handle, PARAMS[name], int(value)), "spo_set_param")
 
     def get_param(self, name: str) -> int:

@@ -21,17 +21,23 @@ def test_algorithmic_bytes_per_eval():
 
 def test_traffic_record_is_dropped_when_kernel_changes(tmp_path, monkeypatch):
     rec = {"kernel_source_sha256_16": bench.kernel_source_digest(),
-           "entries": [{"workload": "w", "storage": "f32", "kind": "vgh", "algo": "brick",
+           "entries": [{"workload": "w", "storage": "f32", "kind": "vgh", "tuning": "brick/t32/v4/s0",
                         "dram_bytes_per_launch": 123}]}
     path = tmp_path / "t.json"
     path.write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
-    assert bench.recorded_traffic("w", "f32", "vgh", "brick") == 123
-    assert bench.recorded_traffic("w", "bf16", "vgh", "brick") is None
-    assert bench.recorded_traffic("w", "f32", "vgh", "gather") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "brick/t32/v4/s0") == 123
+    assert bench.recorded_traffic("w", "bf16", "vgh", "brick/t32/v4/s0") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "gather/t32/v4/s0") is None
     rec["kernel_source_sha256_16"] = "0" * 16
     path.write_text(json.dumps(rec))
-    assert bench.recorded_traffic("w", "f32", "vgh", "brick") is None
+    assert bench.recorded_traffic("w", "f32", "vgh", "brick/t32/v4/s0") is None
+
+
+def test_fp32_peak_is_derived_from_unit_counts_and_clock():
+    tf, src = bench.fp32_peak_tflops(152)
+    assert abs(tf - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-6 or "MEASURED" in src
+    assert "SMs" in src
 
 
 def test_shard_seeds_differ_per_rank():

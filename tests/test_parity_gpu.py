@@ -22,7 +22,8 @@ def torch():
     return t
 
 
-ALGOS = ["gather", "sorted_gather", "brick", "brick4"]
+ALGOS = ["gather", "sorted_gather", "brick", "brick4", "brick_t32", "brick4_t32", "pipe",
+         "pipe_t32"]
 
 
 def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None, algos=("auto",)):
@@ -32,10 +33,13 @@ def gpu_eval(spo, coefs_upload, pos, kind, storage, src_dtype=None, out=None, al
     with spo.OrbitalSet(coefs_upload, storage=storage, src_dtype=src_dtype) as s:
         p = t.from_numpy(np.ascontiguousarray(pos, dtype=np.float32)).cuda()
         for a in algos:
-            if a.startswith("brick") and s.info()["Np"] < 64:
+            s.set_param("brick_vec", 4 if a.startswith("brick4") else 2)
+            s.set_param("brick_tile", 32 if a.endswith("_t32") else 64)
+            s.set_param("brick_schedule", 1 if a.startswith("pipe") else 0)
+            brick = a.startswith("brick") or a.startswith("pipe")
+            if brick and s.info()["Np"] < 32:
                 continue
-            s.set_param("brick_vec", 4 if a == "brick4" else 2)
-            o = s.eval(p, kind, out=out, algo="brick" if a == "brick4" else a)
+            o = s.eval(p, kind, out=out, algo="brick" if brick else a)
             t.cuda.synchronize()
             res[a] = o.cpu().numpy()
         assert spo.device_status() == 0
@@ -264,8 +268,10 @@ def test_kinds_consistent(spo_lib):
 
 
 def test_host_path_matches_device_path(spo_lib):
-    """spo_eval_host (chunked, two streams) gives the device path's bits,
-    including a ragged last chunk."""
+    """spo_eval_host gives the device path's bits: pinned buffers (zero-copy:
+    kernels read and write host memory), pageable buffers (chunked copies on
+    two streams, ragged last chunk), and pinned positions with a pageable
+    output (chunked)."""
     t = torch()
     c = inputs.plane_wave_coefs(8, 8, 8, 384, seed=11).astype(np.float32)
     pos = inputs.wide_positions(10001, 12)   # > 2 chunks of 4369 VGH positions
@@ -274,7 +280,9 @@ def test_host_path_matches_device_path(spo_lib):
         pinned = t.empty((10001, 10, 384), dtype=t.float32).pin_memory()
         host = s.eval_host(t.from_numpy(pos).pin_memory(), "vgh", out=pinned).numpy()
         pageable = s.eval_host(pos, "vgh")
+        mixed = s.eval_host(t.from_numpy(pos).pin_memory(), "vgh")
     assert np.array_equal(dev, host) and np.array_equal(dev, pageable)
+    assert np.array_equal(dev, mixed)
 
 
 def test_deterministic(spo_lib):
@@ -311,11 +319,16 @@ def test_library_conversion_rounds_once_to_nearest_even(spo_lib, storage):
 def test_tuning_parameters(spo_lib):
     c = inputs.uniform_coefs(4, 4, 4, 64, seed=1).astype(np.float32)
     with spo_lib.OrbitalSet(c) as s:
-        assert s.get_param("brick_vec") == 2
-        s.set_param("brick_vec", 4)
         assert s.get_param("brick_vec") == 4
+        s.set_param("brick_vec", 2)
+        assert s.get_param("brick_vec") == 2
         with pytest.raises(spo_lib.SpoError, match="must be 2 or 4"):
             s.set_param("brick_vec", 3)
+        assert s.get_param("brick_tile") == 32
+        s.set_param("brick_tile", 64)
+        assert s.get_param("brick_tile") == 64
+        with pytest.raises(spo_lib.SpoError, match="must be 32 or 64"):
+            s.set_param("brick_tile", 48)
 
 
 def test_footprint_and_padding(spo_lib):
