@@ -357,12 +357,13 @@ def time_kernel(s, pos, out, kind, algo, steps):
 
 def max_rel_diff(a, b, kind):
     """max |a - b| / max |b| per output group (GPU tensors)."""
-    groups = {"v": {"V": [0]}, "vgl": {"V": [0], "G": [1, 2, 3], "L": [4]},
-              "vgh": {"V": [0], "G": [1, 2, 3], "H": [4, 5, 6, 7, 8, 9]}}[kind]
+    groups = {"v": {"V": (0, 1)}, "vgl": {"V": (0, 1), "G": (1, 4), "L": (4, 5)},
+              "vgh": {"V": (0, 1), "G": (1, 4), "H": (4, 10)}}[kind]
     if a.dim() == 2:
         a, b = a[:, None, :], b[:, None, :]
-    return {g: float((a[:, c] - b[:, c]).abs().max() / b[:, c].abs().max().clamp_min(1e-30))
-            for g, c in groups.items()}
+    return {g: float((a[:, lo:hi] - b[:, lo:hi]).abs().max()
+                     / b[:, lo:hi].abs().max().clamp_min(1e-30))
+            for g, (lo, hi) in groups.items()}
 
 
 def run_ours(args):
