@@ -502,6 +502,25 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
                            "table_bytes": sv.footprint(),
                            "max_rel_diff_vs_f32_storage": max_rel_diff(o, ref, kind)}
         res["f32_table_bytes"] = s32.footprint()
+    # fused value + determinant ratio (one row of A^-1 per position)
+    P = pos.shape[0]
+    rows = (2.0 * torch.rand((P, cfg.N), device=pos.device, dtype=torch.float32,
+                             generator=torch.Generator(device=pos.device).manual_seed(7)) - 1.0)
+    ratio = torch.empty((P,), device=pos.device)
+    for _ in range(3):
+        s32.eval_ratio(pos, rows, ratio=ratio)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        s32.eval_ratio(pos, rows, ratio=ratio)
+    e1.record()
+    torch.cuda.synchronize()
+    r_ms = e0.elapsed_time(e1) / steps
+    res["ratio_fused_v"] = {"value": P * cfg.N / (r_ms * 1e-3), "unit": "evals/s",
+                            "ratios_per_s": P / (r_ms * 1e-3), "ms_per_step": round(r_ms, 5),
+                            "what": "spo_eval_ratio: V of all orbitals dotted with an A^-1 row "
+                                    "per position, values not stored"}
     n32 = inputs.NIO32
     c = n32.make_coefs(np.float32)
     p32 = torch.from_numpy(n32.make_positions()).to(pos.device)

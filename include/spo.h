@@ -168,6 +168,30 @@ spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int6
                        float *out, void *stream, spo_algo algo);
 
 /*
+ * spo_eval_ratio — determinant ratios of proposed moves, fused with the
+ * value evaluation (Sec. 3, Alg. 1 "ratio", eq. md_lemma: moving electron k
+ * to r' gives det(A')/det(A) = row k of A^-1 dotted with (phi_1(r'), ...,
+ * phi_N(r')); the non-local pseudopotential quadrature of the local energy
+ * needs the same ratio at several points per electron).
+ *
+ *   pos      device, FP32 [P][3]: the proposed positions.
+ *   rows     device, FP32 [nrows][ld]: rows of A^-1 (orbital index fastest,
+ *            ld >= N).
+ *   row_of   device, int32 [P]: the row of each position (NULL: row p, which
+ *            needs nrows >= P).  Indices outside [0, nrows) are clamped.
+ *   ratio    device, FP32 [P]: rho_p = sum_j rows[row_of[p]][j] phi_j(pos_p).
+ *   v_out    device, FP32 [P][N] or NULL: the values themselves, if wanted.
+ *
+ * The values never go to memory unless v_out asks for them: each thread
+ * multiplies its orbitals' values by the matching row entries and the
+ * partial sums are reduced in a fixed order (deterministic; FP32
+ * accumulation).  Uses the set's per-stream scratch like spo_eval_ex.
+ */
+spo_status spo_eval_ratio(const spo_set *set, const float *pos, int64_t P, const float *rows,
+                          int64_t nrows, int64_t ld, const int32_t *row_of, float *ratio,
+                          float *v_out, void *stream);
+
+/*
  * spo_bin / spo_eval_binned — the two stages of the binned strategies, for
  * callers that evaluate several kinds at the same positions (for example V
  * for the ratio and then VGL for the derivatives of an accepted move, Alg. 1).

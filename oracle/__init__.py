@@ -132,3 +132,27 @@ def condition(coefs: np.ndarray, pos: np.ndarray, kind: int = KIND_VGH,
     if kind == KIND_V:
         return b[:, 0, :]
     return np.concatenate([b[:, :4], (b[:, 4] + b[:, 7] + b[:, 9])[:, None]], axis=1)
+
+
+def spo_ratio(coefs: np.ndarray, pos: np.ndarray, rows: np.ndarray, row_of=None) -> np.ndarray:
+    """Determinant ratios rho_p = sum_j rows[r(p), j] phi_j(pos_p) in FP64.
+
+    arXiv 1708.02645, Sec. 3, eq. md_lemma: moving electron k to r' changes
+    column k of A (A(i,j) = phi_i(r_j)); det(A')/det(A) is the dot product
+    of row k of A^-1 with the orbital values at r'.  rows: [R, N] (the A^-1
+    rows); row_of: [P] row index per position (None: row p).
+    """
+    v = spo_eval(coefs, pos, KIND_V)                        # [P, N], FP64
+    rows = np.asarray(rows, dtype=np.float64)
+    idx = np.arange(v.shape[0]) if row_of is None else np.asarray(row_of)
+    return np.einsum("pj,pj->p", rows[idx], v)
+
+
+def spo_ratio_condition(coefs: np.ndarray, pos: np.ndarray, rows: np.ndarray,
+                        row_of=None) -> np.ndarray:
+    """sum_j |rows[r(p), j]| beta_j(p), with beta the V condition sums: the
+    scale of the rounding error of any FP32 evaluation of the ratio."""
+    b = condition(coefs, pos, KIND_V)
+    rows = np.abs(np.asarray(rows, dtype=np.float64))
+    idx = np.arange(b.shape[0]) if row_of is None else np.asarray(row_of)
+    return np.einsum("pj,pj->p", rows[idx], b)

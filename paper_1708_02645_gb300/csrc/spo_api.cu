@@ -88,8 +88,12 @@ void free_workspace(spo_detail::Workspace &w) {
     cudaFree(w.slots);
     cudaFree(w.perm);
     cudaFree(w.sorted);
+    cudaFree(w.partials);
+    cudaFree(w.vscratch);
     w.counts = w.offsets = w.keys = w.slots = w.perm = nullptr;
     w.sorted = nullptr;
+    w.partials = w.vscratch = nullptr;
+    w.cap_partials = w.cap_vscratch = 0;
     w.cap_positions = w.cap_bins = 0;
 }
 
@@ -107,7 +111,16 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
     if (w->cap_positions < P || w->cap_bins < nbins) {
         const int64_t cp = std::max<int64_t>(P, w->cap_positions);
         const int64_t cb = std::max<int64_t>(nbins, w->cap_bins);
-        free_workspace(*w);   // cudaFree waits for queued work that uses it
+        // cudaFree waits for queued work that uses the old buffers
+        cudaFree(w->counts);
+        cudaFree(w->offsets);
+        cudaFree(w->keys);
+        cudaFree(w->slots);
+        cudaFree(w->perm);
+        cudaFree(w->sorted);
+        w->counts = w->offsets = w->keys = w->slots = w->perm = nullptr;
+        w->sorted = nullptr;
+        w->cap_positions = w->cap_bins = 0;
         if (cudaMalloc(&w->counts, sizeof(int) * cb) != cudaSuccess ||
             cudaMalloc(&w->offsets, sizeof(int) * (cb + 1)) != cudaSuccess ||
             cudaMalloc(&w->keys, sizeof(int) * cp) != cudaSuccess ||
@@ -123,6 +136,22 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
         w->cap_bins = cb;
     }
     *out = w;
+    return SPO_OK;
+}
+
+// Grow a float scratch buffer to `need` elements (cudaFree waits for queued
+// work that still uses the old one).
+spo_status ensure_floats(float **buf, size_t *cap, size_t need) {
+    if (*cap >= need) return SPO_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc(buf, need * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return fail(SPO_ENOMEM, "cudaMalloc of %zu scratch floats failed", need);
+    }
+    *cap = need;
     return SPO_OK;
 }
 
@@ -391,6 +420,62 @@ spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int6
     spo_status s = check_device_eval(set, kind, pos, P, out);
     if (s != SPO_OK || P == 0) return s;
     return eval_queue(set, kind, pos, P, out, static_cast<cudaStream_t>(stream), algo);
+}
+
+spo_status spo_eval_ratio(const spo_set *set, const float *pos, int64_t P, const float *rows,
+                          int64_t nrows, int64_t ld, const int32_t *row_of, float *ratio,
+                          float *v_out, void *stream) {
+    g_last_error[0] = '\0';
+    if (!set) return fail(SPO_EINVAL, "set is NULL");
+    if (P < 0) return fail(SPO_EINVAL, "P = %lld is negative", (long long)P);
+    if (P == 0) return SPO_OK;
+    if (!pos || !rows || !ratio) return fail(SPO_EINVAL, "pos, rows or ratio is NULL");
+    if (nrows < 1 || ld < set->N)
+        return fail(SPO_EINVAL, "need nrows >= 1 and ld >= N (nrows = %lld, ld = %lld)",
+                    (long long)nrows, (long long)ld);
+    if (!row_of && nrows < P) return fail(SPO_EINVAL, "row_of is NULL but nrows < P");
+    if (P > (INT64_C(1) << 40) / set->N) return fail(SPO_EINVAL, "P = %lld too large", (long long)P);
+    DeviceGuard guard(set->device);
+    if (!guard.ok()) return fail(SPO_ECUDA, "cannot select device %d", set->device);
+    spo_status st;
+    if ((st = check_device_pointer(pos, set->device, "pos")) != SPO_OK) return st;
+    if ((st = check_device_pointer(rows, set->device, "rows")) != SPO_OK) return st;
+    if ((st = check_device_pointer(ratio, set->device, "ratio")) != SPO_OK) return st;
+    if (row_of && (st = check_device_pointer(row_of, set->device, "row_of")) != SPO_OK) return st;
+    if (v_out && (st = check_device_pointer(v_out, set->device, "v_out")) != SPO_OK) return st;
+    if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(rows) |
+         reinterpret_cast<uintptr_t>(ratio) | reinterpret_cast<uintptr_t>(row_of) |
+         reinterpret_cast<uintptr_t>(v_out)) & 3)
+        return fail(SPO_EINVAL, "buffers must be 4-byte aligned");
+
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    spo_set *s = const_cast<spo_set *>(set);
+    std::lock_guard<std::mutex> lock(s->mu);
+    spo_detail::RatioArgs ra{rows, row_of, nrows, ld, nullptr, P};
+    cudaError_t e;
+    if (s->has_block_map && choose_algo(s, P) == SPO_ALGO_BRICK) {
+        spo_detail::Workspace *w = nullptr;
+        if ((st = bin_queue(s, pos, P, cs, &w)) != SPO_OK) return st;
+        const int ntiles = spo_detail::brick_tiles_of(s);
+        if ((st = ensure_floats(&w->partials, &w->cap_partials, (size_t)ntiles * P)) != SPO_OK)
+            return st;
+        ra.partials = w->partials;
+        e = spo_detail::launch_brick_ratio(s, *w, P, v_out, ra, cs);
+        if (e == cudaSuccess) e = spo_detail::launch_ratio_reduce(w->partials, ntiles, P, ratio, cs);
+    } else {
+        spo_detail::Workspace *w = nullptr;
+        if ((st = workspace_for(s, cs, P, &w)) != SPO_OK) return st;
+        float *v = v_out;
+        if (!v) {
+            if ((st = ensure_floats(&w->vscratch, &w->cap_vscratch, (size_t)P * s->N)) != SPO_OK)
+                return st;
+            v = w->vscratch;
+        }
+        e = spo_detail::launch_gather(s->storage, SPO_KIND_V, spo_detail::view_of(s), pos, nullptr, P,
+                                      v, cs);
+        if (e == cudaSuccess) e = spo_detail::launch_ratio_dot(v, P, s->N, ra, ratio, cs);
+    }
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "ratio launch");
 }
 
 spo_status spo_bin(const spo_set *set, const float *pos, int64_t P, void *stream) {

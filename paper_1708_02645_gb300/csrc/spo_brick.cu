@@ -49,12 +49,17 @@ struct BrickShape {
     static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
 };
 
-template <typename T, int KIND, int TILE, int V, bool VEC_OUT>
+// RATIO (KIND = V only): each position's values are also multiplied by its
+// row of A^-1 and reduced over the position's lanes; one partial dot product
+// per (tile, position) goes to ra.partials.  out may then be nullptr.
+template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false>
 __global__ void __launch_bounds__(BrickShape<TILE>::threads, BrickShape<TILE>::ctas_per_sm)
 spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
                  int nby, int nbz, int ntiles, int64_t N, const int *__restrict__ offsets,
-                 const float4 *__restrict__ sorted, float *__restrict__ out, int eager)
+                 const float4 *__restrict__ sorted, float *__restrict__ out, int eager,
+                 spo_detail::RatioArgs ra)
 {
+    static_assert(!RATIO || KIND == SPO_KIND_V, "ratios are formed from values");
     constexpr int NC = Rows<KIND>::value;
     constexpr int kThreads = BrickShape<TILE>::threads;
     constexpr int kVec = V;                   // orbitals per thread
@@ -130,7 +135,24 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
                                     base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
                             },
                             acc);
-        if (o0 < N) store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
+        if constexpr (RATIO) {
+            int r = ra.row_of ? __ldg(ra.row_of + p) : p;
+            r = (int)min(max((int64_t)r, (int64_t)0), ra.nrows - 1);
+            const float *arow = ra.rows + (int64_t)r * ra.ld + o0;
+            float dot = 0.0f;
+#pragma unroll
+            for (int k = 0; k < kVec; ++k)
+                if (o0 + k < N) dot = fmaf(acc[0][k], __ldg(arow + k), dot);
+            // the TPP lanes of this position form an aligned group of the warp
+            const unsigned lane = threadIdx.x & 31u;
+            const unsigned gmask = TPP >= 32 ? 0xffffffffu
+                                             : (((1u << TPP) - 1u) << (lane & ~(unsigned)(TPP - 1)));
+#pragma unroll
+            for (int off = TPP / 2; off > 0; off >>= 1) dot += __shfl_xor_sync(gmask, dot, off);
+            if (q == 0) ra.partials[(int64_t)tile * ra.P + p] = dot;
+        }
+        if (o0 < N && (!RATIO || out != nullptr))
+            store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
         cur = nxt;
     }
     if (!ready && threadIdx.x == 0) {
@@ -354,8 +376,40 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
     const int eager = P >= 4 * (int64_t)nbins;   // about 4+ positions per brick
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, out, eager);
+        w.offsets, w.sorted, out, eager, spo_detail::RatioArgs{});
     return cudaGetLastError();
+}
+
+template <typename T, int TILE, int V>
+cudaError_t brick_ratio_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P,
+                               float *out, const spo_detail::RatioArgs &ra, cudaStream_t stream) {
+    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
+    const int nbins = s->nbx * s->nby * s->nbz;
+    const int ntiles = (int)((s->N + TILE - 1) / TILE);
+    const int64_t blocks = (int64_t)nbins * ntiles;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const bool vec_out = out && (s->N % V == 0) && ((reinterpret_cast<uintptr_t>(out) % (4 * V)) == 0);
+    auto kernel = vec_out ? spo_brick_kernel<T, SPO_KIND_V, TILE, V, true, true>
+                          : spo_brick_kernel<T, SPO_KIND_V, TILE, V, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
+    const int eager = P >= 4 * (int64_t)nbins;
+    kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
+        map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
+        w.offsets, w.sorted, out, eager, ra);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t brick_ratio_typed(const spo_set *s, const spo_detail::Workspace &w, int64_t P,
+                              float *out, const spo_detail::RatioArgs &ra, cudaStream_t stream) {
+    const bool v4 = s->brick_vec == 4;
+    if (spo_detail::brick_tile_of(s) == 64)
+        return v4 ? brick_ratio_launch<T, 64, 4>(s, w, P, out, ra, stream)
+                  : brick_ratio_launch<T, 64, 2>(s, w, P, out, ra, stream);
+    return v4 ? brick_ratio_launch<T, 32, 4>(s, w, P, out, ra, stream)
+              : brick_ratio_launch<T, 32, 2>(s, w, P, out, ra, stream);
 }
 
 template <typename T, int KIND, int TILE>
@@ -435,6 +489,21 @@ cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set, c
         case SPO_F16: return brick_kind<__half>(kind, set, w, P, out, stream);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_brick_ratio(const spo_set *set, const Workspace &w, int64_t P, float *out,
+                               const RatioArgs &r, cudaStream_t stream) {
+    switch (set->storage) {
+        case SPO_F32: return brick_ratio_typed<float>(set, w, P, out, r, stream);
+        case SPO_BF16: return brick_ratio_typed<__nv_bfloat16>(set, w, P, out, r, stream);
+        case SPO_F16: return brick_ratio_typed<__half>(set, w, P, out, r, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int brick_tiles_of(const spo_set *s) {
+    const int tile = brick_tile_of(s);
+    return (int)((s->N + tile - 1) / tile);
 }
 
 int brick_tile_of(const spo_set *s) {

@@ -29,6 +29,9 @@ struct Workspace {
     int *slots = nullptr;     // [P]
     int *perm = nullptr;      // [P]
     float4 *sorted = nullptr; // [P]
+    float *partials = nullptr;   // [ratio tiles][P] partial dot products (ratios)
+    float *vscratch = nullptr;   // [P][N] values for the unfused ratio path
+    size_t cap_partials = 0, cap_vscratch = 0;   // floats
     int64_t cap_positions = 0;
     int64_t cap_bins = 0;
     const float *binned_pos = nullptr;   // positions of the last binning
@@ -105,6 +108,31 @@ cudaError_t launch_brick(spo_dtype storage, spo_kind kind, const spo_set *set,
 // [x1-x0][ny][nz][N]) into every padded table row that holds one of them.
 cudaError_t launch_convert(const void *src, spo_dtype src_dtype, int x0, int x1,
                            const spo_set *set, cudaStream_t stream);
+
+// Arguments of the ratio epilogue of the V kernels.
+struct RatioArgs {
+    const float *rows;      // [nrows][ld]
+    const int *row_of;      // [P] or nullptr
+    int64_t nrows, ld;
+    float *partials;        // [ntiles][P]
+    int64_t P;
+};
+
+// Brick kernel for V with the ratio epilogue: per (tile, position) partial
+// dot products into r.partials; values to out unless out is nullptr.
+cudaError_t launch_brick_ratio(const spo_set *set, const Workspace &w, int64_t P, float *out,
+                               const RatioArgs &r, cudaStream_t stream);
+
+// ratio[p] = sum over tiles of partials[t][p], tiles in order.
+cudaError_t launch_ratio_reduce(const float *partials, int ntiles, int64_t P, float *ratio,
+                                cudaStream_t stream);
+
+// ratio[p] = sum_j rows[row_of[p]][j] v[p][j] (one warp per position).
+cudaError_t launch_ratio_dot(const float *v, int64_t P, int64_t N, const RatioArgs &r, float *ratio,
+                             cudaStream_t stream);
+
+// Number of orbital tiles of the brick kernel for a set.
+int brick_tiles_of(const spo_set *set);
 
 // Build the brick kernel's tensor maps for a set (host; driver entry point).
 spo_status make_block_map(spo_set *set);

@@ -43,6 +43,7 @@ SIGNATURES = [
     ("spo_eval_binned", _INT, [_P, _INT, _P, _I64, _P, _P, _INT]),
     ("spo_reserve", _INT, [_P, _I64, _P]),
     ("spo_eval_noalloc", _INT, [_P, _INT, _P, _I64, _P, _P]),
+    ("spo_eval_ratio", _INT, [_P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _P]),
     ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_set_param", _INT, [_P, _INT, _I64]),
@@ -250,6 +251,31 @@ class OrbitalSet:
                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream), a),
                "spo_eval_binned")
         return out
+
+    def eval_ratio(self, pos, rows, row_of=None, ratio=None, v_out=None, stream=None):
+        """Determinant ratios rho_p = rows[row_of[p]] . phi(pos_p) (eq.
+        md_lemma).  rows: FP32 CUDA [R, ld >= N]; row_of: int32 CUDA [P] or
+        None (row p); v_out: optional FP32 CUDA [P, N] for the values."""
+        torch = _torch()
+        P = self._check_pos(pos)
+        if not (rows.is_cuda and rows.dtype == torch.float32 and rows.dim() == 2
+                and rows.stride(1) == 1):
+            raise TypeError("rows must be a row-major float32 CUDA matrix")
+        if row_of is not None and not (row_of.is_cuda and row_of.dtype == torch.int32
+                                       and row_of.is_contiguous() and row_of.numel() == P):
+            raise TypeError("row_of must be a contiguous int32 CUDA vector of length P")
+        if ratio is None:
+            ratio = torch.empty((P,), dtype=torch.float32, device=pos.device)
+        if v_out is not None:
+            v_out = self._out_for(pos, P, KIND_V, v_out)
+        _check(load().spo_eval_ratio(
+            self.handle, ctypes.c_void_p(pos.data_ptr()), P, ctypes.c_void_p(rows.data_ptr()),
+            int(rows.shape[0]), int(rows.stride(0)),
+            ctypes.c_void_p(row_of.data_ptr() if row_of is not None else None),
+            ctypes.c_void_p(ratio.data_ptr()),
+            ctypes.c_void_p(v_out.data_ptr() if v_out is not None else None),
+            _stream_handle(stream)), "spo_eval_ratio")
+        return ratio
 
     def eval_noalloc(self, pos, kind="vgh", out=None, stream=None):
         """spo_eval_noalloc: the library allocates nothing (pass `out` to

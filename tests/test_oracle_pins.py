@@ -328,3 +328,34 @@ def test_oracle_empty_inputs(oracle_lib):
     assert out.shape == (0, 10, 2)
     out = oracle.spo_eval(np.zeros((4, 4, 4, 0)), np.zeros((3, 3)))
     assert out.shape == (3, 10, 0)
+
+
+def test_ratio_is_the_determinant_ratio(oracle_lib):
+    """eq. md_lemma: with A(i, j) = phi_i(r_j), moving electron k to r' gives
+    det(A') / det(A) = (row k of A^-1) . phi(r').  Checked against
+    numpy.linalg.det on the spline's own orbital matrix."""
+    import oracle
+    ns, N = (7, 6, 8), 9
+    c = inputs.uniform_coefs(*ns, N, seed=51)
+    r = inputs.uniform_positions(N, seed=52).astype(np.float64)      # N electrons
+    A = oracle.spo_eval(c, r, KIND_V).T                               # A[i, j] = phi_i(r_j)
+    Ainv = np.linalg.inv(A)
+    moves = inputs.wide_positions(N, seed=53).astype(np.float64)     # r'_k for each k
+    rho = oracle.spo_ratio(c, moves, Ainv, row_of=np.arange(N))       # row k for move k
+    phi_new = oracle.spo_eval(c, moves, KIND_V)                       # [k, i]
+    for k in range(N):
+        A2 = A.copy()
+        A2[:, k] = phi_new[k]
+        exact = np.linalg.det(A2) / np.linalg.det(A)
+        assert abs(rho[k] - exact) < 1e-9 * max(1.0, abs(exact)), (k, rho[k], exact)
+
+
+def test_ratio_reduces_to_values_for_unit_rows(oracle_lib):
+    import oracle
+    c = inputs.uniform_coefs(5, 5, 6, 4, seed=54)
+    pos = inputs.wide_positions(12, seed=55).astype(np.float64)
+    v = oracle.spo_eval(c, pos, KIND_V)
+    eye = np.eye(4)
+    for j in range(4):
+        rho = oracle.spo_ratio(c, pos, eye[j:j + 1], row_of=np.zeros(12, dtype=int))
+        assert np.array_equal(rho, v[:, j])
