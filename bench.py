@@ -521,6 +521,9 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
                             "ratios_per_s": P / (r_ms * 1e-3), "ms_per_step": round(r_ms, 5),
                             "what": "spo_eval_ratio: V of all orbitals dotted with an A^-1 row "
                                     "per position, values not stored"}
+    res["autotune"] = s32.autotune(kind, pos.shape[0])
+    configure(s32, args)   # back to the command line's tuning
+    res["crowd"] = measure_crowd(args, kind, steps)
     n32 = inputs.NIO32
     c = n32.make_coefs(np.float32)
     p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
@@ -533,6 +536,56 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
             res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
                                        "ms_per_step": round(step_ms, 5), "algo": a}
     return res
+
+
+def measure_crowd(args, kind, steps):
+    """Batched crowds: 3 orbital sets (32^3/64, 48^3/192, 64^3/384, FP32),
+    512 walkers with U{64..768} electrons, walker w on set w mod 3; one graph
+    replay per step (binning + one brick-kernel launch over all sets)."""
+    import torch
+    from paper_1708_02645_gb300 import spo
+    cr = inputs.CROWD
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sets = [spo.OrbitalSet(cr.make_coefs(k, np.float32)) for k in range(len(cr.sets))]
+    sizes = cr.sizes()
+    which = cr.set_of_walker()
+    items, evals = [], 0
+    for w in range(cr.walkers):
+        k = int(which[w])
+        p = torch.from_numpy(cr.make_positions(w, int(sizes[w]))).to(dev)
+        o = torch.empty(sets[k].out_shape(p.shape[0], kind), dtype=torch.float32, device=dev)
+        items.append((k, p, o))
+        evals += p.shape[0] * sets[k].N
+    total = int(sizes.sum())
+    out = {"workload": cr.name, "walkers": cr.walkers, "positions": total,
+           "sets": [list(x) for x in cr.sets], "evals_per_step": evals}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / n
+
+    with spo.Batch(sets, total, cr.walkers) as b:
+        b.graph(items, kind)
+        g_ms = timed(b.launch, steps)
+        e_ms = timed(lambda: b.eval(items, kind), steps)
+    w_ms = timed(lambda: [sets[k].eval(p, kind, out=o) for k, p, o in items], max(1, steps // 10))
+    out.update({"value": evals / (g_ms * 1e-3), "unit": "evals/s",
+                "graph_ms_per_step": round(g_ms, 5), "batch_eval_ms_per_step": round(e_ms, 5),
+                "per_walker_calls_ms_per_step": round(w_ms, 5),
+                "gpu_launches_per_step": "1 graph (item_of, count, scan, scatter, brick kernel "
+                                         "+ 1 memset)"})
+    for st in sets:
+        st.close()
+    return out
 
 
 def run_reference(args):

@@ -232,6 +232,53 @@ spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, 
 spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
                             float *out, void *stream);
 
+/*
+ * Batched crowds — many walkers, each with its own positions and output,
+ * against several orbital sets, in one binning and one evaluation launch
+ * (Sec. 4.1 and Alg. 1: a population of walkers is advanced together; the
+ * paper's outlook, Sec. 6.5, proposes running over table tiles in parallel).
+ *
+ * spo_work describes one walker: `set` indexes the plan's sets, pos is device
+ * FP32 [P][3], out device FP32 [P][rows][N of that set].
+ *
+ * spo_batch_create(sets, nsets, max_positions, max_items, &plan): a plan over
+ *   up to SPO_BATCH_MAX_SETS sets of one storage type (the sets must outlive
+ *   the plan; each needs >= 32 padded orbitals).  The plan allocates all
+ *   scratch for up to max_positions positions in up to max_items walkers, so
+ *   evaluations allocate nothing.
+ * spo_batch_eval(plan, kind, items, nitems, stream): copies the item table
+ *   to the device and queues the evaluation of every walker on `stream`
+ *   (one binning over all sets' bricks, one launch of the brick kernel over
+ *   every (set, brick, orbital tile)).  Asynchronous; items may be reused or
+ *   freed on return.
+ * spo_batch_graph(plan, kind, items, nitems, stream): records the same work
+ *   for these items into a CUDA graph held by the plan (the item table is
+ *   copied first, synchronously); spo_batch_launch(plan, stream) replays it.
+ *   Between replays the caller may change the contents of the pos buffers
+ *   (new moves), not the items themselves.
+ * Calls on one plan must be ordered (one stream): they share its scratch.
+ */
+#define SPO_BATCH_MAX_SETS 8
+
+typedef struct {
+    int32_t set;
+    int32_t reserved;   /* 0 */
+    int64_t P;
+    const float *pos;
+    float *out;
+} spo_work;
+
+typedef struct spo_batch spo_batch;
+
+spo_status spo_batch_create(const spo_set *const *sets, int nsets, int64_t max_positions,
+                            int max_items, spo_batch **out);
+spo_status spo_batch_eval(spo_batch *plan, spo_kind kind, const spo_work *items, int nitems,
+                          void *stream);
+spo_status spo_batch_graph(spo_batch *plan, spo_kind kind, const spo_work *items, int nitems,
+                           void *stream);
+spo_status spo_batch_launch(spo_batch *plan, void *stream);
+spo_status spo_batch_destroy(spo_batch *plan);
+
 /* Allocate (or grow) the set's scratch for `stream` to hold batches of up to
  * P positions, so that later evaluations on that stream allocate nothing.
  * Synchronous. */
@@ -259,6 +306,28 @@ spo_status spo_device_status(unsigned int *flags, int clear, void *stream);
  */
 spo_status spo_eval_host(spo_set *set, spo_kind kind, const float *pos_host, int64_t P,
                          float *out_host, void *stream);
+
+/*
+ * spo_autotune — time the evaluation strategies and tunings for this set,
+ * kind and batch size on the set's device (synthetic uniform positions, CUDA
+ * events on `stream`), apply the fastest (its tile, orbitals per thread and
+ * schedule become the set's parameters, and SPO_ALGO_AUTO uses its strategy
+ * for batches within a factor 4 of P) and report it in *best.  Results are
+ * cached per (grid, N, storage, kind, power-of-two bucket of P, SM count)
+ * for the process and, if the environment variable SPO_TUNE_CACHE names a
+ * file, in that file (one line per key), so that later processes skip the
+ * timing.  Allocates temporary device memory; synchronous.
+ */
+typedef struct {
+    int32_t algo;            /* spo_algo */
+    int32_t brick_tile;
+    int32_t brick_vec;
+    int32_t brick_schedule;
+    float ms;                /* time of one evaluation with this choice */
+    int32_t from_cache;      /* 1 if no timing was needed */
+} spo_tuning;
+
+spo_status spo_autotune(spo_set *set, spo_kind kind, int64_t P, void *stream, spo_tuning *best);
 
 /* Set or read a tuning parameter.  Tuning changes speed only: every value
  * gives bit-identical outputs.  Invalid parameters or values: SPO_EINVAL.

@@ -208,7 +208,13 @@ spo_status check_binned_algo(const spo_set *set, spo_algo algo) {
 // Queue one evaluation (arguments already checked; device already current).
 spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
                       cudaStream_t stream, spo_algo algo) {
-    if (algo == SPO_ALGO_AUTO) algo = choose_algo(set, P);
+    if (algo == SPO_ALGO_AUTO) {
+        const int k = (int)kind;
+        const int64_t tp = set->tuned_P[k];
+        algo = (set->tuned_algo[k] != 0 && P * 4 >= tp && P <= tp * 4)
+                   ? static_cast<spo_algo>(set->tuned_algo[k])
+                   : choose_algo(set, P);
+    }
     if (algo == SPO_ALGO_GATHER) {
         cudaError_t e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
                                                   nullptr, P, out, stream);
@@ -239,6 +245,11 @@ spo_status check_device_eval(const spo_set *set, spo_kind kind, const float *pos
 }  // namespace
 
 namespace spo_detail {
+
+spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
+                      cudaStream_t stream, spo_algo algo) {
+    return ::eval_queue(set, kind, pos, P, out, stream, algo);
+}
 
 spo_status fail(spo_status status, const char *fmt, ...) {
     va_list ap;

@@ -10,6 +10,7 @@
 //
 // The order inside a brick depends on atomic arrival order; every output of
 // a position depends only on that position, so results are unaffected.
+#include "spo_batch.h"
 #include "spo_device.cuh"
 #include "spo_internal.h"
 
@@ -106,6 +107,11 @@ __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__r
 
 namespace spo_detail {
 
+cudaError_t launch_scan(const int *counts, int *offsets, int n, cudaStream_t stream) {
+    bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(counts, offsets, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int nbx, int nby,
                        int nbz, Workspace &w, cudaStream_t stream) {
     const int nbins = nbx * nby * nbz;
@@ -116,7 +122,8 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, grid_axis(nx), grid_axis(ny),
                                                      grid_axis(nz), nby, nbz, w.counts, w.keys,
                                                      w.slots);
-    bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(w.counts, w.offsets, nbins);
+    e = launch_scan(w.counts, w.offsets, nbins, stream);
+    if (e != cudaSuccess) return e;
     bin_scatter_kernel<<<blocks, threads, 0, stream>>>(pos, w.keys, w.slots, w.offsets, w.perm,
                                                        w.sorted, P);
     return cudaGetLastError();

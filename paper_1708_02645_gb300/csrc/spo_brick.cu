@@ -26,6 +26,7 @@
 
 #include <algorithm>
 
+#include "spo_batch.h"
 #include "spo_device.cuh"
 #include "spo_internal.h"
 #include "spo_tma.cuh"
@@ -535,6 +536,13 @@ spo_status make_block_map(spo_set *s) {
     }
     s->has_block_map = true;
     return SPO_OK;
+}
+
+cudaError_t device_status_address(unsigned int **addr) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_spo_device_status);
+    *addr = static_cast<unsigned int *>(p);
+    return e;
 }
 
 cudaError_t read_device_status(unsigned int *flags, bool clear, cudaStream_t stream) {

@@ -1,0 +1,208 @@
+// Brick kernel over a batch of walkers and orbital sets: one CTA per
+// (set, brick, orbital tile) unit of the whole batch.  The sets' tensor maps
+// and shapes arrive in one __grid_constant__ parameter block; positions come
+// as sorted records from the batch binning, each with the address of its own
+// output rows (every walker has its own output buffer).  The per-position
+// arithmetic is the single-set brick kernel's (spo_device.cuh), so a
+// walker's outputs are bit-identical to an spo_eval of that walker alone.
+#include <cuda.h>
+
+#include <algorithm>
+
+#include "spo_batch.h"
+#include "spo_device.cuh"
+#include "spo_internal.h"
+#include "spo_tma.cuh"
+
+namespace {
+
+using namespace spo_dev;
+using spo_detail::BatchParams;
+using spo_detail::BatchSetDesc;
+using spo_detail::kBlockEdge;
+using spo_detail::kBrick;
+
+constexpr int kBlockRows = kBlockEdge * kBlockEdge * kBlockEdge;   // 343
+constexpr int kVec = 4;
+
+template <int TILE>
+struct Shape {
+    static constexpr int threads = TILE >= 64 ? 256 : 128;
+    static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
+};
+
+template <typename T, int KIND, int TILE, bool VEC_OUT>
+__global__ void __launch_bounds__(Shape<TILE>::threads, Shape<TILE>::ctas_per_sm)
+spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__restrict__ offsets,
+                       const float4 *__restrict__ sorted, float *const *__restrict__ dst,
+                       unsigned int *status)
+{
+    constexpr int NC = Rows<KIND>::value;
+    constexpr int kThreads = Shape<TILE>::threads;
+    constexpr int TPP = TILE / kVec;
+    constexpr int PPR = kThreads / TPP;
+    constexpr uint32_t kBytes = kBlockRows * TILE * sizeof(T);
+    extern __shared__ __align__(128) unsigned char smem[];
+    T *block = reinterpret_cast<T *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBytes);
+
+    const int unit = blockIdx.x;
+    int s = 0;
+    while (s + 1 < bp.nsets && unit >= bp.sets[s + 1].unit_base) ++s;
+    const BatchSetDesc &d = bp.sets[s];
+    const int local = unit - d.unit_base;
+    const int lbrick = local / d.ntiles, tile = local - lbrick * d.ntiles;
+    const int bz = lbrick % d.nbz, by = (lbrick / d.nbz) % d.nby, bx = lbrick / (d.nbz * d.nby);
+    const int gbrick = d.brick_base + lbrick;
+    const uint32_t bar_s = smem_addr(bar);
+
+    int begin = 0, end = 0;
+    if (!bp.eager) {
+        begin = __ldg(offsets + gbrick);
+        end = __ldg(offsets + gbrick + 1);
+        if (begin == end) return;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(bar_s, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(bar_s, kBytes);
+        tma_load_4d(smem_addr(block), &bp.maps[s], bar_s, tile * TILE, bz * kBrick, by * kBrick,
+                    bx * kBrick);
+    }
+    if (bp.eager) {
+        begin = __ldg(offsets + gbrick);
+        end = __ldg(offsets + gbrick + 1);
+    }
+    __syncthreads();
+    if (begin == end) {
+        if (threadIdx.x == 0 && !mbar_wait_bounded(bar_s, 0)) atomicOr(status, 1u);
+        return;
+    }
+
+    const int q = threadIdx.x % TPP;
+    const int64_t N = d.N;
+    const int64_t o0 = (int64_t)tile * TILE + q * kVec;
+    int i = begin + threadIdx.x / TPP;
+    float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float *ocur = i < end ? dst[i] : nullptr;
+    bool ready = false;
+    for (; i < end; i += PPR) {
+        const bool more = i + PPR < end;
+        const float4 nxt = more ? __ldg(sorted + i + PPR) : cur;
+        float *onxt = more ? dst[i + PPR] : ocur;
+        XAxis X;
+        Axis Y, Z;
+        make_xaxis(cur.x, d.gx, X);
+        make_axis(cur.y, d.gy, Y);
+        make_axis(cur.z, d.gz, Z);
+        if (!ready) {
+            if (!mbar_wait_bounded(bar_s, 0)) {
+                atomicOr(status, 1u);
+                return;
+            }
+            ready = true;
+        }
+        const int lx = min(max(X.cell - bx * kBrick, 0), kBrick - 1);
+        const int ly = min(max(Y.cell - by * kBrick, 0), kBrick - 1);
+        const int lz = min(max(Z.cell - bz * kBrick, 0), kBrick - 1);
+        const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
+        float acc[NC][kVec];
+        window_reduce<KIND, kVec, true>(X, d.gx, Y, Z,
+                            [&](int a, int b, int g, float *v) {
+                                load_coefs<T, kVec, false>(
+                                    base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
+                            },
+                            acc);
+        if (o0 < N) store_rows<NC, kVec, VEC_OUT>(ocur + o0, N, N - o0, acc);
+        cur = nxt;
+        ocur = onxt;
+    }
+    if (!ready && threadIdx.x == 0 && !mbar_wait_bounded(bar_s, 0)) atomicOr(status, 1u);
+}
+
+template <typename T, int KIND, int TILE>
+cudaError_t launch_typed(const BatchParams &bp, const int *offsets, const float4 *sorted,
+                         float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
+    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
+    auto kernel = vec_out ? spo_brick_batch_kernel<T, KIND, TILE, true>
+                          : spo_brick_batch_kernel<T, KIND, TILE, false>;
+    if (bp.total_units <= 0) return cudaSuccess;
+    kernel<<<(unsigned)bp.total_units, Shape<TILE>::threads, kSmem, stream>>>(bp, offsets, sorted, dst,
+                                                                             status);
+    return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+cudaError_t launch_tile(int tile, const BatchParams &bp, const int *offsets, const float4 *sorted,
+                        float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
+    return tile == 64 ? launch_typed<T, KIND, 64>(bp, offsets, sorted, dst, vec_out, status, stream)
+                      : launch_typed<T, KIND, 32>(bp, offsets, sorted, dst, vec_out, status, stream);
+}
+
+template <typename T>
+cudaError_t launch_kind(spo_kind kind, int tile, const BatchParams &bp, const int *offsets,
+                        const float4 *sorted, float *const *dst, bool vec_out, unsigned int *status,
+                        cudaStream_t stream) {
+    switch (kind) {
+        case SPO_KIND_V:
+            return launch_tile<T, SPO_KIND_V>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+        case SPO_KIND_VGL:
+            return launch_tile<T, SPO_KIND_VGL>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+        case SPO_KIND_VGH:
+            return launch_tile<T, SPO_KIND_VGH>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int KIND>
+cudaError_t prepare_kind() {
+    cudaError_t e = cudaSuccess;
+    const int s32 = (int)((size_t)kBlockRows * 32 * sizeof(T) + 16);
+    const int s64 = (int)((size_t)kBlockRows * 64 * sizeof(T) + 16);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 64, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 64, false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    return e;
+}
+
+template <typename T>
+cudaError_t prepare_type() {
+    cudaError_t e = prepare_kind<T, SPO_KIND_V>();
+    if (e == cudaSuccess) e = prepare_kind<T, SPO_KIND_VGL>();
+    if (e == cudaSuccess) e = prepare_kind<T, SPO_KIND_VGH>();
+    return e;
+}
+
+}  // namespace
+
+namespace spo_detail {
+
+cudaError_t prepare_brick_batch() {
+    cudaError_t e = prepare_type<float>();
+    if (e == cudaSuccess) e = prepare_type<__nv_bfloat16>();
+    if (e == cudaSuccess) e = prepare_type<__half>();
+    return e;
+}
+
+cudaError_t launch_brick_batch(spo_dtype storage, spo_kind kind, int tile, const BatchParams &bp,
+                               const int *offsets, const float4 *sorted, float *const *dst,
+                               bool vec_out, unsigned int *status, cudaStream_t stream) {
+    switch (storage) {
+        case SPO_F32:
+            return launch_kind<float>(kind, tile, bp, offsets, sorted, dst, vec_out, status, stream);
+        case SPO_BF16:
+            return launch_kind<__nv_bfloat16>(kind, tile, bp, offsets, sorted, dst, vec_out, status,
+                                              stream);
+        case SPO_F16:
+            return launch_kind<__half>(kind, tile, bp, offsets, sorted, dst, vec_out, status, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace spo_detail

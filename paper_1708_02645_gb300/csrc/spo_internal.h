@@ -55,6 +55,9 @@ struct spo_set {
     int brick_tile = 32;     // orbitals per brick-kernel tile (32 or 64)
     int brick_schedule = 0;  // 0: one CTA per (brick, tile); 1: persistent pipelined CTAs
     int num_sms = 0;         // multiprocessors of the set's device
+    // strategy chosen by spo_autotune for each kind, for batches near tuned_P
+    int tuned_algo[3] = {0, 0, 0};
+    int64_t tuned_P[3] = {0, 0, 0};
     CUtensorMap block_map[2];   // 4-D TMA maps of the table, boxes (32 | 64, 7, 7, 7)
     bool has_block_map = false; // Np >= 32: the brick kernel can serve this set
 
@@ -75,6 +78,11 @@ namespace spo_detail {
 
 // Records a formatted message for spo_last_error() and returns `status`.
 spo_status fail(spo_status status, const char *fmt, ...);
+
+// Queue one evaluation with explicit strategy (arguments checked, device
+// current); SPO_ALGO_AUTO resolves through the set's tuning.
+spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
+                      cudaStream_t stream, spo_algo algo);
 
 // Geometry of one table as the kernels see it.
 struct TableView {

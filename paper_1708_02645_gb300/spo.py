@@ -44,6 +44,12 @@ SIGNATURES = [
     ("spo_reserve", _INT, [_P, _I64, _P]),
     ("spo_eval_noalloc", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_eval_ratio", _INT, [_P, _P, _I64, _P, _I64, _I64, _P, _P, _P, _P]),
+    ("spo_autotune", _INT, [_P, _INT, _I64, _P, _P]),
+    ("spo_batch_create", _INT, [_P, _INT, _I64, _INT, ctypes.POINTER(_P)]),
+    ("spo_batch_eval", _INT, [_P, _INT, _P, _INT, _P]),
+    ("spo_batch_graph", _INT, [_P, _INT, _P, _INT, _P]),
+    ("spo_batch_launch", _INT, [_P, _P]),
+    ("spo_batch_destroy", _INT, [_P]),
     ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_set_param", _INT, [_P, _INT, _I64]),
@@ -139,6 +145,15 @@ def device_status(clear: bool = True, stream=None) -> int:
     return int(flags.value)
 
 
+class _Tuning(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("brick_tile", ctypes.c_int32),
+                ("brick_vec", ctypes.c_int32), ("brick_schedule", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("from_cache", ctypes.c_int32)]
+
+
+ALGO_NAMES = {v: k for k, v in ALGOS.items()}
+
+
 class OrbitalSet:
     """One B-spline orbital set resident on the current CUDA device.
 
@@ -188,6 +203,16 @@ class OrbitalSet:
         v = _I64()
         _check(load().spo_get_param(self.handle, PARAMS[name], ctypes.byref(v)), "spo_get_param")
         return int(v.value)
+
+    def autotune(self, kind="vgh", P: int = 98304, stream=None) -> dict:
+        """spo_autotune: time the strategies for this kind and batch size,
+        apply the fastest, and return it."""
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        t = _Tuning()
+        _check(load().spo_autotune(self.handle, k, int(P), _stream_handle(stream), ctypes.byref(t)),
+               "spo_autotune")
+        return {"algo": ALGO_NAMES[t.algo], "brick_tile": t.brick_tile, "brick_vec": t.brick_vec,
+                "brick_schedule": t.brick_schedule, "ms": t.ms, "from_cache": bool(t.from_cache)}
 
     def footprint(self) -> int:
         b = ctypes.c_size_t()
@@ -332,6 +357,68 @@ class OrbitalSet:
     def close(self):
         if getattr(self, "_h", None) is not None:
             _check(load().spo_destroy(self._h), "spo_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _Work(ctypes.Structure):
+    _fields_ = [("set", ctypes.c_int32), ("reserved", ctypes.c_int32), ("P", ctypes.c_int64),
+                ("pos", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+class Batch:
+    """A batched-crowd plan over several OrbitalSets (same storage type):
+    many walkers, each (set index, pos [P, 3] CUDA FP32, out CUDA FP32),
+    evaluated with one binning and one kernel launch, optionally recorded
+    into a CUDA graph and replayed."""
+
+    def __init__(self, sets, max_positions: int, max_items: int):
+        self.sets = list(sets)          # keep the sets alive
+        arr = (ctypes.c_void_p * len(self.sets))(*[s.handle.value for s in self.sets])
+        h = ctypes.c_void_p()
+        _check(load().spo_batch_create(arr, len(self.sets), int(max_positions), int(max_items),
+                                       ctypes.byref(h)), "spo_batch_create")
+        self._h = h
+
+    def _table(self, items):
+        table = (_Work * max(1, len(items)))()
+        for i, (k, pos, out) in enumerate(items):
+            table[i].set = int(k)
+            table[i].reserved = 0
+            table[i].P = int(pos.shape[0])
+            table[i].pos = pos.data_ptr()
+            table[i].out = out.data_ptr()
+        return table
+
+    def eval(self, items, kind="vgh", stream=None):
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        table = self._table(items)
+        _check(load().spo_batch_eval(self._h, k, table, len(items), _stream_handle(stream)),
+               "spo_batch_eval")
+
+    def graph(self, items, kind="vgh", stream=None):
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        table = self._table(items)
+        _check(load().spo_batch_graph(self._h, k, table, len(items), _stream_handle(stream)),
+               "spo_batch_graph")
+
+    def launch(self, stream=None):
+        _check(load().spo_batch_launch(self._h, _stream_handle(stream)), "spo_batch_launch")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().spo_batch_destroy(self._h), "spo_batch_destroy")
             self._h = None
 
     def __del__(self):

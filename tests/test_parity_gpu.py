@@ -375,3 +375,24 @@ def test_nio32_errors_reported(spo_lib, oracle_lib):
     ref = oracle.spo_eval(c, pos.astype(np.float64), 1)
     e = errors(got, ref, 1)
     assert all(v["max_rel"] < 1e-5 for v in e.values()), e
+
+
+def test_autotune_picks_a_strategy_and_keeps_outputs(spo_lib, tmp_path, monkeypatch):
+    """spo_autotune times the strategies, applies the fastest (outputs stay
+    bit-identical), caches the result in the process and in SPO_TUNE_CACHE."""
+    t = torch()
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SPO_TUNE_CACHE", str(cache))
+    c = inputs.plane_wave_coefs(20, 18, 22, 72, seed=27).astype(np.float32)
+    pos = t.from_numpy(inputs.uniform_positions(6000, 28)).cuda()
+    with spo_lib.OrbitalSet(c) as s:
+        before = s.eval(pos, "vgl", algo="gather")
+        best = s.autotune("vgl", 6000)
+        assert best["algo"] in ("gather", "sorted_gather", "brick") and best["ms"] > 0
+        assert not best["from_cache"]
+        after = s.eval(pos, "vgl")                     # AUTO now follows the tuning
+        t.cuda.synchronize()
+        assert t.equal(before, after)
+        again = s.autotune("vgl", 7000)                # same power-of-two bucket
+        assert again["from_cache"] and again["algo"] == best["algo"]
+    assert cache.exists() and "kind=1" in cache.read_text()
