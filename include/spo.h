@@ -279,6 +279,69 @@ spo_status spo_batch_graph(spo_batch *plan, spo_kind kind, const spo_work *items
 spo_status spo_batch_launch(spo_batch *plan, void *stream);
 spo_status spo_batch_destroy(spo_batch *plan);
 
+/*
+ * Learned surrogate — a small learned function of the position standing in
+ * for the B-spline table, aimed at the memory footprint the paper attacks
+ * (Sec. 6.3-6.4: memory per walker and up to 3.8x smaller runs); the
+ * B-spline stays its teacher and the judge of its error.  The paper has no
+ * such surrogate; this is one of the patterns built on the path.
+ *
+ * Function: a periodic multiresolution hashed grid (levels l with
+ * resolutions R_l geometric from r_min to r_max; 2^log2_table entries of
+ * `features` features per level; corners indexed densely when R_l^3 fits
+ * the table, else by the spatial hash (i ^ 2654435761 j ^ 805459861 k);
+ * C2 quintic interpolation weights) feeding `layers` softplus layers of
+ * width `hidden` and a linear layer of N outputs.  Values, gradients and
+ * Laplacians are carried through the network as five channels, so the
+ * outputs have the VGL layout [P][5][N] (V: [P][N]).
+ *
+ * spo_surrogate_create(spec, seed, &s): FP32 master parameters initialised
+ *   from splitmix64 streams (grid U(-1e-4, 1e-4), weights U(+-1/sqrt(in)),
+ *   biases 0), Adam moments, and inference copies (grid FP16, weights BF16).
+ * spo_surrogate_train(s, teacher, steps, batch, lr, channel_weights, seed,
+ *   stream, &last_loss): each step draws `batch` uniform positions
+ *   (coordinate i of step t: the top 24 bits of splitmix64(seed + (3 batch t
+ *   + i + 1) 0x9E3779B97F4A7C15) over 2^24), evaluates the teacher's VGL
+ *   for them (the spline kernels), and takes one Adam step on sum_c w_c
+ *   mean((out_c - target_c)^2).  channel_weights = 5 floats (V, Gx, Gy, Gz,
+ *   L) or NULL for 1 / mean(target_c^2) of the first batch.  The teacher must
+ *   have the same N.  Synchronous; refreshes the inference copies.
+ * spo_surrogate_eval(s, kind, pos, P, out, precision, stream): kind V or
+ *   VGL; precision 0 evaluates the FP32 master parameters (CUDA cores),
+ *   precision 1 the inference copies (FP16 grid, BF16 weights and
+ *   activations, FP32 accumulation on the tcgen05 tensor cores).
+ * spo_surrogate_grad(s, pos, target, P, channel_weights, &loss, grid, W, b,
+ *   stream): loss and its gradient with respect to every FP32 master
+ *   parameter for P device positions [P][3] and device targets [P][5][N]
+ *   (same channel weights rule), written to host arrays laid out as in
+ *   spo_surrogate_params.  Leaves the parameters unchanged; synchronous.
+ * spo_surrogate_footprint(s, &bytes): device bytes of the inference copies.
+ * spo_surrogate_params(s, grid, W, b, to_device): copy all FP32 master
+ *   parameters from (to_device != 0) or to host arrays: grid
+ *   [levels][2^log2_table][features]; W[l] [out][in]; b[l] [out]
+ *   (layers + 1 entries each).  Setting them refreshes the inference copies.
+ */
+typedef struct {
+    int32_t levels, log2_table, features, r_min, r_max, hidden, layers, reserved;
+    int64_t N;
+} spo_surrogate_spec;
+
+typedef struct spo_surrogate spo_surrogate;
+
+spo_status spo_surrogate_create(const spo_surrogate_spec *spec, uint64_t seed, spo_surrogate **out);
+spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t steps, int64_t batch,
+                               float lr, const float *channel_weights, uint64_t seed, void *stream,
+                               float *last_loss);
+spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos, int64_t P,
+                              float *out, int precision, void *stream);
+spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *target, int64_t P,
+                              const float *channel_weights, float *loss, float *grid, float *const *W,
+                              float *const *b, void *stream);
+spo_status spo_surrogate_footprint(const spo_surrogate *s, size_t *bytes);
+spo_status spo_surrogate_params(spo_surrogate *s, float *grid, float *const *W, float *const *b,
+                                int to_device);
+spo_status spo_surrogate_destroy(spo_surrogate *s);
+
 /* Allocate (or grow) the set's scratch for `stream` to hold batches of up to
  * P positions, so that later evaluations on that stream allocate nothing.
  * Synchronous. */

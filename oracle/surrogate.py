@@ -137,13 +137,36 @@ def softplus(z):
     return sp, sg, sg * (1.0 - sg), sg * (1.0 - sg) * (1.0 - 2.0 * sg)
 
 
-def forward(params: SurrogateParams, pos):
-    """Surrogate outputs [P, 5, N] (V, Gx, Gy, Gz, L) and the intermediates."""
+def round_bf16(x):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even)."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)                     # x = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def round_fp16(x):
+    """Round to the nearest IEEE binary16 (ties to even, subnormals kept)."""
+    return np.asarray(x, dtype=np.float64).astype(np.float16).astype(np.float64)
+
+
+def quantised(params: SurrogateParams) -> SurrogateParams:
+    """The inference copy: grid in binary16, weights in bfloat16, biases
+    as they are."""
+    return SurrogateParams(params.spec, round_fp16(params.grid), [round_bf16(w) for w in params.W],
+                           [np.array(b) for b in params.b])
+
+
+def forward(params: SurrogateParams, pos, act_round=None):
+    """Surrogate outputs [P, 5, N] (V, Gx, Gy, Gz, L) and the intermediates.
+    act_round, if given, is applied to every layer's input (all channels):
+    the inference precision rounds activations to bfloat16 there."""
     h, enc_cache = encode(params, pos)
     acts = [h]
     pre = []
     nl = len(params.W)
     for l in range(nl):
+        if act_round is not None:
+            h = act_round(h)
         z = np.einsum("pci,oi->pco", h, params.W[l])
         z[:, 0, :] += params.b[l]
         pre.append(z)
@@ -215,3 +238,9 @@ def init_params(spec: SurrogateSpec, seed: int = 0, grid_scale: float = 1e-4):
         W.append((2.0 * u - 1.0) / math.sqrt(fan_in))
         b.append(np.zeros(widths[l + 1]))
     return SurrogateParams(spec, grid, W, b)
+
+
+def as_float32(params: SurrogateParams) -> SurrogateParams:
+    """The parameters rounded to FP32 (what a device copy holds), in FP64."""
+    f = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return SurrogateParams(params.spec, f(params.grid), [f(w) for w in params.W], [f(b) for b in params.b])

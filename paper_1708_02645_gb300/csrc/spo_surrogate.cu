@@ -1,0 +1,835 @@
+// Learned surrogate of an orbital set: periodic multiresolution hashed grid
+// + softplus perceptron, with value / gradient / Laplacian carried through
+// the network as five channels (the function is specified in include/spo.h).
+//
+// Training (FP32 master parameters, CUDA cores): each step samples uniform
+// positions, asks the spline (the teacher) for their VGL, runs the forward
+// pass with channels, the loss, the hand-derived backward (encode, GEMMs,
+// softplus jets) and one Adam step.  Inference (precision 1) uses an FP16
+// grid and BF16 weights; its perceptron runs on the tcgen05 tensor cores
+// (spo_surrogate_mma.cu); precision 0 evaluates the FP32 master parameters.
+//
+// Activations are stored as [P][5][width] (row = position x channel), so a
+// linear layer is one GEMM over 5 P rows with the bias added to the value
+// rows only.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spo.h"
+#include "spo_internal.h"
+#include "spo_surrogate.h"
+#include "spo_surrogate_enc.cuh"
+
+namespace {
+
+using spo_detail::fail;
+using spo_detail::SurrLevels;
+using spo_dev::level_corners;
+
+constexpr int kMaxLayers = 8;   // weight matrices (hidden layers + output)
+
+// ---------------------------------------------------------------------------
+// encoding (level geometry and corner weights: spo_surrogate_enc.cuh)
+// ---------------------------------------------------------------------------
+template <typename TG>
+__device__ __forceinline__ float grid_val(const TG *g, size_t i);
+template <>
+__device__ __forceinline__ float grid_val<float>(const float *g, size_t i) { return __ldg(g + i); }
+template <>
+__device__ __forceinline__ float grid_val<__half>(const __half *g, size_t i) { return __half2float(g[i]); }
+
+// e[p][ch][l F + f]; one thread per (position, level)
+template <typename TG>
+__global__ void encode_fwd_kernel(const TG *__restrict__ grid, SurrLevels lv, const float *__restrict__ pos,
+                                  int64_t P, float *__restrict__ e) {
+    const int L = lv.levels, F = lv.features;
+    const int W = L * F;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = it / L;
+        const int l = (int)(it - p * L);
+        float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
+        uint32_t slot[8];
+        float cw[5][8];
+        level_corners(r, lv.R[l], lv.dense[l] != 0, lv.mask, slot, cw);
+        const TG *gl = grid + (size_t)l * lv.table * F;
+        for (int f = 0; f < F; ++f) {
+            float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float th = grid_val<TG>(gl, (size_t)slot[q] * F + f);
+#pragma unroll
+                for (int ch = 0; ch < 5; ++ch) acc[ch] = fmaf(cw[ch][q], th, acc[ch]);
+            }
+#pragma unroll
+            for (int ch = 0; ch < 5; ++ch) e[(p * 5 + ch) * W + l * F + f] = acc[ch];
+        }
+    }
+}
+
+// g_grid[l][slot][f] += sum_ch cw[ch][q] ge[p][ch][l F + f]
+__global__ void encode_bwd_kernel(SurrLevels lv, const float *__restrict__ pos, int64_t P,
+                                  const float *__restrict__ ge, float *__restrict__ g_grid) {
+    const int L = lv.levels, F = lv.features;
+    const int W = L * F;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = it / L;
+        const int l = (int)(it - p * L);
+        float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
+        uint32_t slot[8];
+        float cw[5][8];
+        level_corners(r, lv.R[l], lv.dense[l] != 0, lv.mask, slot, cw);
+        float *gl = g_grid + (size_t)l * lv.table * F;
+        for (int f = 0; f < F; ++f) {
+            float g[5];
+#pragma unroll
+            for (int ch = 0; ch < 5; ++ch) g[ch] = __ldg(ge + (p * 5 + ch) * W + l * F + f);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v = 0.0f;
+#pragma unroll
+                for (int ch = 0; ch < 5; ++ch) v = fmaf(cw[ch][q], g[ch], v);
+                atomicAdd(gl + (size_t)slot[q] * F + f, v);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 tiled GEMMs (CUDA cores): C[i][j] = sum_k A(i, k) B(k, j)
+// ---------------------------------------------------------------------------
+constexpr int TM = 64, TN = 64, TK = 16;
+
+// mode 0 (forward):   A(i,k) = X[i][k] (ld K),  B(k,j) = Wt[j][k] (ld K);  C[i][j] (ld N) = . + bias on value rows
+// mode 1 (back data): A(i,k) = G[i][k] (ld K),  B(k,j) = Wt[k][j] (ld N);  C[i][j]
+// mode 2 (weights):   A(i,k) = G[k][i] (ld M),  B(k,j) = X[k][j] (ld N);  C[i][j] += (split-K, atomics)
+// BF16 (mode 0 only): A rounded to BF16, B read as BF16.
+template <int MODE, bool BF16>
+__global__ void __launch_bounds__(256)
+gemm_kernel(const float *__restrict__ A, const void *__restrict__ Bv, float *__restrict__ C,
+            const float *__restrict__ bias, int M, int N, int K, int lda, int ldb, int k_chunk) {
+    __shared__ float As[TK][TM + 1];
+    __shared__ float Bs[TK][TN + 1];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * TM, j0 = blockIdx.y * TN;   // row tiles on x: 5 P rows can exceed 65535 tiles
+    const int kbeg = blockIdx.z * k_chunk, kend = min(K, kbeg + k_chunk);
+    float acc[4][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += TK) {
+        for (int e = threadIdx.x; e < TM * TK; e += 256) {
+            const int ii = e / TK, kk = e % TK;   // (used by modes 0 and 1)
+            int i, k;
+            float v = 0.0f;
+            if (MODE == 2) {
+                const int ii2 = e % TM, kk2 = e / TM;
+                i = i0 + ii2;
+                k = k0 + kk2;
+                if (i < M && k < kend) v = __ldg(A + (int64_t)k * lda + i);
+                As[kk2][ii2] = v;
+            } else {
+                i = i0 + ii;
+                k = k0 + kk;
+                if (i < M && k < kend) v = __ldg(A + (int64_t)i * lda + k);
+                if (BF16) v = __bfloat162float(__float2bfloat16_rn(v));
+                As[kk][ii] = v;
+            }
+        }
+        for (int e = threadIdx.x; e < TK * TN; e += 256) {
+            float v = 0.0f;
+            if (MODE == 0) {
+                const int jj = e / TK, kk = e % TK;
+                const int j = j0 + jj, k = k0 + kk;
+                if (j < N && k < kend)
+                    v = BF16 ? __bfloat162float(static_cast<const __nv_bfloat16 *>(Bv)[(int64_t)j * ldb + k])
+                             : __ldg(static_cast<const float *>(Bv) + (int64_t)j * ldb + k);
+                Bs[kk][jj] = v;
+            } else {
+                const int jj = e % TN, kk = e / TN;
+                const int j = j0 + jj, k = k0 + kk;
+                if (j < N && k < kend) v = __ldg(static_cast<const float *>(Bv) + (int64_t)k * ldb + j);
+                Bs[kk][jj] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) a[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) b[u] = Bs[kk][tx * 4 + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u;
+        if (i >= M) continue;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = j0 + tx * 4 + v;
+            if (j >= N) continue;
+            if (MODE == 2) {
+                atomicAdd(C + (int64_t)i * N + j, acc[u][v]);
+            } else {
+                float r = acc[u][v];
+                if (MODE == 0 && bias && i % 5 == 0) r += __ldg(bias + j);
+                C[(int64_t)i * N + j] = r;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// softplus with channels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void softplus_d(float z, float &sp, float &d1, float &d2, float &d3) {
+    sp = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
+    const float sg = 1.0f / (1.0f + expf(-z));
+    d1 = sg;
+    d2 = sg * (1.0f - sg);
+    d3 = d2 * (1.0f - 2.0f * sg);
+}
+
+__global__ void act_fwd_kernel(const float *__restrict__ z, float *__restrict__ h, int64_t P, int W) {
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * W;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = it / W;
+        const int j = (int)(it - p * W);
+        const float *zp = z + p * 5 * W + j;
+        float sp, d1, d2, d3;
+        softplus_d(zp[0], sp, d1, d2, d3);
+        const float gx = zp[W], gy = zp[2 * W], gz = zp[3 * W], lz = zp[4 * W];
+        float *hp = h + p * 5 * W + j;
+        hp[0] = sp;
+        hp[W] = d1 * gx;
+        hp[2 * W] = d1 * gy;
+        hp[3 * W] = d1 * gz;
+        hp[4 * W] = d2 * (gx * gx + gy * gy + gz * gz) + d1 * lz;
+    }
+}
+
+__global__ void act_bwd_kernel(const float *__restrict__ z, const float *__restrict__ g,
+                               float *__restrict__ gz, int64_t P, int W) {
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * W;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = it / W;
+        const int j = (int)(it - p * W);
+        const float *zp = z + p * 5 * W + j;
+        const float *gp = g + p * 5 * W + j;
+        float sp, d1, d2, d3;
+        softplus_d(zp[0], sp, d1, d2, d3);
+        const float zx = zp[W], zy = zp[2 * W], zz = zp[3 * W], zl = zp[4 * W];
+        const float g0 = gp[0], gxv = gp[W], gyv = gp[2 * W], gzv = gp[3 * W], gl = gp[4 * W];
+        const float g2 = zx * zx + zy * zy + zz * zz;
+        float *o = gz + p * 5 * W + j;
+        o[0] = g0 * d1 + (gxv * zx + gyv * zy + gzv * zz) * d2 + gl * (d3 * g2 + d2 * zl);
+        o[W] = gxv * d1 + 2.0f * gl * d2 * zx;
+        o[2 * W] = gyv * d1 + 2.0f * gl * d2 * zy;
+        o[3 * W] = gzv * d1 + 2.0f * gl * d2 * zz;
+        o[4 * W] = gl * d1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// loss, bias gradient, Adam, sampling, quantisation
+// ---------------------------------------------------------------------------
+struct ChannelWeights {
+    float w[5];
+};
+
+// g = 2 w_c (out - target) / (P N); loss accumulated in FP64
+__global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ target, int64_t P,
+                            int64_t N, ChannelWeights cw, float *__restrict__ g, double *loss) {
+    __shared__ double red[256];
+    double local = 0.0;
+    const double inv = 1.0 / ((double)P * (double)N);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P * 5 * N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)((e / N) % 5);
+        const float d = out[e] - target[e];
+        g[e] = (float)(2.0 * cw.w[ch] * d * inv);
+        local += (double)cw.w[ch] * d * d * inv;
+    }
+    red[threadIdx.x] = local;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+}
+
+// mean of target_c^2 over positions and orbitals, per channel (sums in FP64)
+__global__ void channel_power_kernel(const float *__restrict__ target, int64_t P, int64_t N,
+                                     double *pw) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P * 5 * N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int ch = (int)((e / N) % 5);
+        const double v = target[e];
+        atomicAdd(pw + ch, v * v);
+    }
+}
+
+// gb[j] += sum_p gz[p][0][j]; blockIdx.y takes a slice of the positions
+__global__ void bias_grad_kernel(const float *__restrict__ gz, int64_t P, int W, float *__restrict__ gb) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= W) return;
+    const int64_t per = (P + gridDim.y - 1) / gridDim.y;
+    const int64_t p0 = (int64_t)blockIdx.y * per, p1 = min(P, p0 + per);
+    float s = 0.0f;
+    for (int64_t p = p0; p < p1; ++p) s += __ldg(gz + p * 5 * W + j);
+    atomicAdd(gb + j, s);
+}
+
+__global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        g[i] = 0.0f;
+    }
+}
+
+// uniform positions in the unit cube, splitmix64 on (seed, counter)
+__global__ void sample_kernel(float *pos, int64_t n3, unsigned long long seed, unsigned long long base) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (base + (unsigned long long)i + 1ull) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        pos[i] = (float)(z >> 40) * (1.0f / 16777216.0f);
+    }
+}
+
+__global__ void to_half_kernel(const float *__restrict__ a, __half *__restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2half_rn(a[i]);
+}
+
+__global__ void to_bf16_kernel(const float *__restrict__ a, __nv_bfloat16 *__restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// a[i] = (2 u_i - 1) * mul (div == 0) or (2 u_i - 1) / div, u_i the 53-bit
+// uniform of splitmix64(seed, counter i + 1), in FP64 rounded once to FP32
+__global__ void uniform_init_kernel(float *a, int64_t n, unsigned long long seed, double mul, double div) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double v = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+        a[i] = (float)(div != 0.0 ? v / div : v * mul);
+    }
+}
+
+int blocks_for(int64_t n, int threads = 256) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 16));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the object
+// ---------------------------------------------------------------------------
+struct spo_surrogate {
+    int device = 0;
+    spo_surrogate_spec spec{};
+    int nl = 0;                      // weight matrices
+    int widths[kMaxLayers + 1] = {};
+    SurrLevels lv{};
+    int64_t grid_n = 0;              // levels * T * F
+
+    // FP32 master parameters, gradients and Adam moments: one flat buffer
+    // each, [grid | W0 | b0 | W1 | b1 | ...]
+    float *param = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    int64_t nparam = 0;
+    int64_t w_off[kMaxLayers] = {}, b_off[kMaxLayers] = {};
+    int64_t adam_t = 0;
+
+    // inference copies
+    __half *grid16 = nullptr;
+    __nv_bfloat16 *w16 = nullptr;    // all weight matrices back to back
+    int64_t w16_off[kMaxLayers] = {};
+    int64_t w16_n = 0;
+
+    // scratch (grown): positions, targets, per-layer activations and
+    // pre-activations, two gradient buffers
+    float *pos = nullptr, *target = nullptr;
+    float *act[kMaxLayers + 1] = {}, *pre[kMaxLayers] = {};
+    float *gbuf[2] = {};
+    double *dacc = nullptr;          // loss and channel powers
+    int64_t cap_P = 0;
+
+    bool use_tc = false;   // the fused tensor-core kernel serves precision 1
+    int num_sms = 0;
+};
+
+namespace {
+
+void free_scratch(spo_surrogate *s) {
+    cudaFree(s->pos);
+    cudaFree(s->target);
+    for (auto &a : s->act) { cudaFree(a); a = nullptr; }
+    for (auto &a : s->pre) { cudaFree(a); a = nullptr; }
+    for (auto &a : s->gbuf) { cudaFree(a); a = nullptr; }
+    s->pos = s->target = nullptr;
+    s->cap_P = 0;
+}
+
+spo_status grow_scratch(spo_surrogate *s, int64_t P) {
+    if (s->cap_P >= P) return SPO_OK;
+    free_scratch(s);
+    const int wmax = *std::max_element(s->widths, s->widths + s->nl + 1);
+    cudaError_t e = cudaMalloc(&s->pos, sizeof(float) * 3 * (size_t)P);
+    if (e == cudaSuccess) e = cudaMalloc(&s->target, sizeof(float) * 5 * (size_t)P * s->spec.N);
+    for (int l = 0; l <= s->nl && e == cudaSuccess; ++l)
+        e = cudaMalloc(&s->act[l], sizeof(float) * 5 * (size_t)P * s->widths[l]);
+    for (int l = 0; l < s->nl && e == cudaSuccess; ++l)
+        e = cudaMalloc(&s->pre[l], sizeof(float) * 5 * (size_t)P * s->widths[l + 1]);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = cudaMalloc(&s->gbuf[k], sizeof(float) * 5 * (size_t)P * wmax);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_scratch(s);
+        return fail(SPO_ENOMEM, "surrogate scratch for %lld positions failed", (long long)P);
+    }
+    s->cap_P = P;
+    return SPO_OK;
+}
+
+cudaError_t gemm(int mode, bool bf16, const float *A, const void *B, float *C, const float *bias, int M,
+                 int N, int K, int lda, int ldb, cudaStream_t st) {
+    if (mode == 2) {
+        // C[N_out][K_in] += sum over M rows: split the row range across CTAs
+        const int chunks = std::max(1, std::min(256, (K + 4095) / 4096));
+        const int k_chunk = ((K + chunks - 1) / chunks + TK - 1) / TK * TK;
+        dim3 g((M + TM - 1) / TM, (N + TN - 1) / TN, (K + k_chunk - 1) / k_chunk);
+        gemm_kernel<2, false><<<g, 256, 0, st>>>(A, B, C, bias, M, N, K, lda, ldb, k_chunk);
+    } else {
+        dim3 g((M + TM - 1) / TM, (N + TN - 1) / TN, 1);
+        if (mode == 0 && bf16)
+            gemm_kernel<0, true><<<g, 256, 0, st>>>(A, B, C, bias, M, N, K, lda, ldb, K);
+        else if (mode == 0)
+            gemm_kernel<0, false><<<g, 256, 0, st>>>(A, B, C, bias, M, N, K, lda, ldb, K);
+        else
+            gemm_kernel<1, false><<<g, 256, 0, st>>>(A, B, C, bias, M, N, K, lda, ldb, K);
+    }
+    return cudaGetLastError();
+}
+
+// Forward pass with the FP32 master parameters over P positions in s->pos
+// (or `pos`), leaving activations in s->act / s->pre; returns the output.
+cudaError_t forward_fp32(spo_surrogate *s, const float *pos, int64_t P, float *out, cudaStream_t st) {
+    cudaError_t e;
+    encode_fwd_kernel<float><<<blocks_for(P * s->lv.levels), 256, 0, st>>>(s->param, s->lv, pos, P,
+                                                                             s->act[0]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int M = (int)(5 * P);
+    for (int l = 0; l < s->nl; ++l) {
+        const int in = s->widths[l], o = s->widths[l + 1];
+        float *z = (l == s->nl - 1 && out) ? out : s->pre[l];
+        e = gemm(0, false, s->act[l], s->param + s->w_off[l], z, s->param + s->b_off[l], M, o, in, in,
+                 in, st);
+        if (e != cudaSuccess) return e;
+        if (l < s->nl - 1) {
+            act_fwd_kernel<<<blocks_for(P * o), 256, 0, st>>>(z, s->act[l + 1], P, o);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+void refresh_inference(spo_surrogate *s, cudaStream_t st) {
+    to_half_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grid16, s->grid_n);
+    for (int l = 0; l < s->nl; ++l) {
+        const int64_t n = (int64_t)s->widths[l] * s->widths[l + 1];
+        to_bf16_kernel<<<blocks_for(n), 256, 0, st>>>(s->param + s->w_off[l], s->w16 + s->w16_off[l], n);
+    }
+}
+
+// Channel weights of the loss: given, else 1 / mean(target_c^2) of `target`.
+cudaError_t channel_weights_for(spo_surrogate *s, const float *target, int64_t P, const float *given,
+                                ChannelWeights &cw, cudaStream_t st) {
+    if (given) {
+        for (int c = 0; c < 5; ++c) cw.w[c] = given[c];
+        return cudaSuccess;
+    }
+    const int64_t N = s->spec.N;
+    cudaError_t e = cudaMemsetAsync(s->dacc, 0, sizeof(double) * 8, st);
+    if (e != cudaSuccess) return e;
+    channel_power_kernel<<<blocks_for(P * 5 * N), 256, 0, st>>>(target, P, N, s->dacc);
+    double pw[8];
+    e = cudaMemcpyAsync(pw, s->dacc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (int c = 0; c < 5; ++c) {
+        const double mean = pw[c] / ((double)P * N);
+        cw.w[c] = mean > 0 ? (float)(1.0 / mean) : 1.0f;
+    }
+    return e;
+}
+
+// Forward, loss (into dacc[0]) and backward over P positions; the gradient
+// is added to s->grad.
+cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, int64_t P,
+                     const ChannelWeights &cw, cudaStream_t st) {
+    const int64_t N = s->spec.N;
+    const int M = (int)(5 * P);
+    float *out = s->gbuf[0];   // network output [P][5][N] (gbuf holds max width >= N columns)
+    cudaError_t e = forward_fp32(s, pos, P, out, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->dacc, 0, sizeof(double), st);
+    if (e == cudaSuccess) {
+        loss_kernel<<<blocks_for(P * 5 * N), 256, 0, st>>>(out, target, P, N, cw, s->gbuf[1], s->dacc);
+        e = cudaGetLastError();
+    }
+    // g = gbuf[gi] is d loss / d output of layer l; the two buffers alternate
+    int gi = 1;
+    for (int l = s->nl - 1; l >= 0 && e == cudaSuccess; --l) {
+        const int in = s->widths[l], o = s->widths[l + 1];
+        float *gz = s->gbuf[gi];
+        if (l < s->nl - 1) {   // through the softplus of layer l
+            gz = s->gbuf[1 - gi];
+            act_bwd_kernel<<<blocks_for(P * o), 256, 0, st>>>(s->pre[l], s->gbuf[gi], gz, P, o);
+            e = cudaGetLastError();
+            gi = 1 - gi;
+        }
+        if (e == cudaSuccess)
+            e = gemm(2, false, gz, s->act[l], s->grad + s->w_off[l], nullptr, o, in, M, o, in, st);
+        if (e == cudaSuccess) {
+            bias_grad_kernel<<<dim3((o + 127) / 128, (unsigned)std::min<int64_t>(P, 256)), 128, 0, st>>>(
+                gz, P, o, s->grad + s->b_off[l]);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {   // d loss / d input of layer l
+            e = gemm(1, false, gz, s->param + s->w_off[l], s->gbuf[1 - gi], nullptr, M, in, o, o, in, st);
+            gi = 1 - gi;
+        }
+    }
+    if (e == cudaSuccess) {
+        encode_bwd_kernel<<<blocks_for(P * s->lv.levels), 256, 0, st>>>(s->lv, pos, P, s->gbuf[gi], s->grad);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int device) {
+        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
+        if (prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev_ >= 0) cudaSetDevice(prev_);
+    }
+    bool ok() const { return ok_; }
+
+  private:
+    int prev_ = -1;
+    bool ok_ = true;
+};
+
+spo_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(SPO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+}  // namespace
+
+namespace spo_detail {
+
+// Inference forward on the CUDA cores (FP16 grid, BF16 weights and layer
+// inputs, FP32 accumulation): the reading the fused tensor-core kernel
+// follows, used for networks that kernel does not serve.
+cudaError_t surrogate_forward_inference(spo_surrogate *s, const float *pos, int64_t P, float *out,
+                                        cudaStream_t st) {
+    cudaError_t e;
+    encode_fwd_kernel<__half><<<blocks_for(P * s->lv.levels), 256, 0, st>>>(s->grid16, s->lv, pos, P,
+                                                                              s->act[0]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int M = (int)(5 * P);
+    for (int l = 0; l < s->nl; ++l) {
+        const int in = s->widths[l], o = s->widths[l + 1];
+        float *z = (l == s->nl - 1) ? out : s->pre[l];
+        e = gemm(0, true, s->act[l], s->w16 + s->w16_off[l], z, s->param + s->b_off[l], M, o, in, in, in, st);
+        if (e != cudaSuccess) return e;
+        if (l < s->nl - 1) {
+            act_fwd_kernel<<<blocks_for(P * o), 256, 0, st>>>(z, s->act[l + 1], P, o);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+SurrMlpView mlp_view(const spo_surrogate *s) {
+    SurrMlpView v;
+    v.nl = s->nl;
+    for (int l = 0; l <= s->nl; ++l) v.widths[l] = s->widths[l];
+    for (int l = 0; l < s->nl; ++l) {
+        v.W[l] = s->w16 + s->w16_off[l];
+        v.b[l] = s->param + s->b_off[l];
+    }
+    return v;
+}
+
+}  // namespace spo_detail
+
+extern "C" {
+
+spo_status spo_surrogate_create(const spo_surrogate_spec *spec, uint64_t seed, spo_surrogate **out) {
+    fail(SPO_OK, "");
+    if (!spec || !out) return fail(SPO_EINVAL, "spec or out is NULL");
+    *out = nullptr;
+    if (spec->levels < 1 || spec->levels > spo_detail::kSurrMaxLevels || spec->log2_table < 4 ||
+        spec->log2_table > 24 || spec->features < 1 || spec->features > 4 || spec->r_min < 2 ||
+        spec->r_max < spec->r_min || spec->r_max > (1 << 20) || spec->hidden < 1 ||
+        spec->hidden > 1024 || spec->layers < 1 || spec->layers > kMaxLayers - 1 || spec->N < 1 ||
+        spec->N > 4096)
+        return fail(SPO_EINVAL, "surrogate spec out of range");
+    spo_surrogate *s = new (std::nothrow) spo_surrogate();
+    if (!s) return fail(SPO_ENOMEM, "host allocation failed");
+    cudaGetDevice(&s->device);
+    s->spec = *spec;
+    s->nl = spec->layers + 1;
+    s->widths[0] = spec->levels * spec->features;
+    for (int l = 1; l <= spec->layers; ++l) s->widths[l] = spec->hidden;
+    s->widths[s->nl] = (int)spec->N;
+    // level resolutions: floor(r_min b^l), b = (r_max / r_min)^(1 / (levels - 1))
+    s->lv.levels = spec->levels;
+    s->lv.features = spec->features;
+    s->lv.table = 1 << spec->log2_table;
+    s->lv.mask = (uint32_t)s->lv.table - 1u;
+    const double b = spec->levels > 1 ? std::pow((double)spec->r_max / spec->r_min, 1.0 / (spec->levels - 1)) : 1.0;
+    for (int l = 0; l < spec->levels; ++l) {
+        const int R = (int)std::floor(spec->r_min * std::pow(b, l) + 1e-9);
+        s->lv.R[l] = R;
+        s->lv.dense[l] = (int64_t)R * R * R <= (int64_t)s->lv.table;
+    }
+    s->grid_n = (int64_t)spec->levels * s->lv.table * spec->features;
+    int64_t off = s->grid_n, w16 = 0;
+    for (int l = 0; l < s->nl; ++l) {
+        s->w_off[l] = off;
+        off += (int64_t)s->widths[l] * s->widths[l + 1];
+        s->b_off[l] = off;
+        off += s->widths[l + 1];
+        s->w16_off[l] = w16;
+        w16 += (int64_t)s->widths[l] * s->widths[l + 1];
+    }
+    s->nparam = off;
+    s->w16_n = w16;
+    {
+        spo_detail::SurrMlpView v;
+        v.nl = s->nl;
+        for (int l = 0; l <= s->nl; ++l) v.widths[l] = s->widths[l];
+        s->use_tc = spo_detail::surrogate_tc_supported(v, s->lv);
+    }
+    DeviceGuard guard(s->device);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+    cudaError_t e = cudaMalloc(&s->param, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&s->grad, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&s->m1, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&s->m2, sizeof(float) * off);
+    if (e == cudaSuccess) e = cudaMalloc(&s->grid16, sizeof(__half) * s->grid_n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->w16, sizeof(__nv_bfloat16) * w16);
+    if (e == cudaSuccess) e = cudaMalloc(&s->dacc, sizeof(double) * 8);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
+        cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc);
+        delete s;
+        return fail(SPO_ENOMEM, "surrogate parameter allocation failed");
+    }
+    cudaStream_t st = nullptr;
+    uniform_init_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grid_n, seed, 1e-4, 0.0);
+    for (int l = 0; l < s->nl; ++l) {
+        const int64_t n = (int64_t)s->widths[l] * s->widths[l + 1];
+        uniform_init_kernel<<<blocks_for(n), 256, 0, st>>>(s->param + s->w_off[l], n,
+                                                            seed + 1 + (uint64_t)l, 0.0,
+                                                            std::sqrt((double)s->widths[l]));
+    }
+    for (int l = 0; l < s->nl; ++l) cudaMemsetAsync(s->param + s->b_off[l], 0, sizeof(float) * s->widths[l + 1], st);
+    cudaMemsetAsync(s->grad, 0, sizeof(float) * off, st);
+    cudaMemsetAsync(s->m1, 0, sizeof(float) * off, st);
+    cudaMemsetAsync(s->m2, 0, sizeof(float) * off, st);
+    refresh_inference(s, st);
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        spo_surrogate_destroy(s);
+        return cuda_fail(e, "surrogate initialisation");
+    }
+    *out = s;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_destroy(spo_surrogate *s) {
+    if (!s) return SPO_OK;
+    DeviceGuard guard(s->device);
+    cudaDeviceSynchronize();
+    free_scratch(s);
+    cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
+    cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc);
+    delete s;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_footprint(const spo_surrogate *s, size_t *bytes) {
+    if (!s || !bytes) return fail(SPO_EINVAL, "surrogate or bytes is NULL");
+    int64_t biases = 0;
+    for (int l = 0; l < s->nl; ++l) biases += s->widths[l + 1];
+    *bytes = sizeof(__half) * s->grid_n + sizeof(__nv_bfloat16) * s->w16_n + sizeof(float) * biases;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_params(spo_surrogate *s, float *grid, float *const *W, float *const *b,
+                                int to_device) {
+    fail(SPO_OK, "");
+    if (!s || !grid || !W || !b) return fail(SPO_EINVAL, "NULL argument");
+    DeviceGuard guard(s->device);
+    const cudaMemcpyKind k = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    auto cp = [&](float *dev, float *host, int64_t n) {
+        return to_device ? cudaMemcpy(dev, host, sizeof(float) * n, k)
+                         : cudaMemcpy(host, dev, sizeof(float) * n, k);
+    };
+    cudaError_t e = cp(s->param, grid, s->grid_n);
+    for (int l = 0; l < s->nl && e == cudaSuccess; ++l) {
+        e = cp(s->param + s->w_off[l], W[l], (int64_t)s->widths[l] * s->widths[l + 1]);
+        if (e == cudaSuccess) e = cp(s->param + s->b_off[l], b[l], s->widths[l + 1]);
+    }
+    if (e == cudaSuccess && to_device) {
+        refresh_inference(s, nullptr);
+        e = cudaDeviceSynchronize();
+    }
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "parameter copy");
+}
+
+spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos, int64_t P, float *out,
+                              int precision, void *stream) {
+    fail(SPO_OK, "");
+    if (!s) return fail(SPO_EINVAL, "surrogate is NULL");
+    if (kind != SPO_KIND_V && kind != SPO_KIND_VGL)
+        return fail(SPO_EUNSUPPORTED, "the surrogate gives V or VGL");
+    if (P < 0 || P > (INT64_C(1) << 26)) return fail(SPO_EINVAL, "P out of range");
+    if (P == 0) return SPO_OK;
+    if (!pos || !out) return fail(SPO_EINVAL, "pos or out is NULL");
+    if (precision != 0 && precision != 1) return fail(SPO_EINVAL, "precision must be 0 or 1");
+    DeviceGuard guard(s->device);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (precision == 1 && s->use_tc) {   // one fused launch, no scratch
+        const cudaError_t e = spo_detail::surrogate_fused_tc(spo_detail::mlp_view(s), s->grid16, s->lv, pos, P,
+                                                             out, kind == SPO_KIND_V, s->num_sms, st);
+        return e == cudaSuccess ? SPO_OK : cuda_fail(e, "fused surrogate evaluation");
+    }
+    // evaluate in chunks of at most 65536 positions (bounded scratch)
+    const int64_t chunk = std::min<int64_t>(P, 65536);
+    spo_status rs = grow_scratch(s, chunk);
+    if (rs != SPO_OK) return rs;
+    const int64_t N = s->spec.N;
+    cudaError_t e = cudaSuccess;
+    for (int64_t p0 = 0; p0 < P && e == cudaSuccess; p0 += chunk) {
+        const int64_t np = std::min(chunk, P - p0);
+        float *dst = kind == SPO_KIND_VGL ? out + p0 * 5 * N : s->target;
+        e = precision == 0 ? forward_fp32(s, pos + 3 * p0, np, dst, st)
+                           : spo_detail::surrogate_forward_inference(s, pos + 3 * p0, np, dst, st);
+        if (e == cudaSuccess && kind == SPO_KIND_V)   // value rows only
+            e = cudaMemcpy2DAsync(out + p0 * N, sizeof(float) * N, s->target, sizeof(float) * 5 * N,
+                                  sizeof(float) * N, np, cudaMemcpyDeviceToDevice, st);
+    }
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate evaluation");
+}
+
+spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *target, int64_t P,
+                              const float *channel_weights, float *loss, float *grid, float *const *W,
+                              float *const *b, void *stream) {
+    fail(SPO_OK, "");
+    if (!s || !pos || !target || !grid || !W || !b) return fail(SPO_EINVAL, "NULL argument");
+    if (P < 1 || P > (1 << 20)) return fail(SPO_EINVAL, "need 1 <= P <= 2^20");
+    DeviceGuard guard(s->device);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    spo_status rs = grow_scratch(s, P);
+    if (rs != SPO_OK) return rs;
+    ChannelWeights cw{};
+    cudaError_t e = channel_weights_for(s, target, P, channel_weights, cw, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->grad, 0, sizeof(float) * s->nparam, st);
+    if (e == cudaSuccess) e = backward(s, pos, target, P, cw, st);
+    double loss_h = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss_h, s->dacc, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grid, s->grad, sizeof(float) * s->grid_n, cudaMemcpyDeviceToHost, st);
+    for (int l = 0; l < s->nl && e == cudaSuccess; ++l) {
+        e = cudaMemcpyAsync(W[l], s->grad + s->w_off[l], sizeof(float) * s->widths[l] * s->widths[l + 1],
+                            cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b[l], s->grad + s->b_off[l], sizeof(float) * s->widths[l + 1],
+                                cudaMemcpyDeviceToHost, st);
+    }
+    // training expects the gradient buffer zeroed between steps
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->grad, 0, sizeof(float) * s->nparam, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (loss) *loss = (float)loss_h;
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate gradient");
+}
+
+spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t steps, int64_t batch,
+                               float lr, const float *channel_weights, uint64_t seed, void *stream,
+                               float *last_loss) {
+    fail(SPO_OK, "");
+    if (!s || !teacher) return fail(SPO_EINVAL, "surrogate or teacher is NULL");
+    if (teacher->N != s->spec.N) return fail(SPO_EINVAL, "teacher has N = %lld, surrogate %lld",
+                                             (long long)teacher->N, (long long)s->spec.N);
+    if (steps < 0 || batch < 1 || batch > (1 << 20) || !(lr > 0.0f))
+        return fail(SPO_EINVAL, "need steps >= 0, 1 <= batch <= 2^20, lr > 0");
+    DeviceGuard guard(s->device);
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    spo_status rs = grow_scratch(s, batch);
+    if (rs != SPO_OK) return rs;
+    const int64_t P = batch;
+    ChannelWeights cw{};
+    double loss_h = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (int64_t step = 0; step < steps && e == cudaSuccess; ++step) {
+        sample_kernel<<<blocks_for(3 * P), 256, 0, st>>>(s->pos, 3 * P, seed,
+                                                           (unsigned long long)step * 3 * P);
+        spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->pos, P, s->target, st, SPO_ALGO_AUTO);
+        if (es != SPO_OK) return es;
+        if (step == 0) e = channel_weights_for(s, s->target, P, channel_weights, cw, st);
+        if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st);
+        if (e == cudaSuccess) {
+            ++s->adam_t;
+            const float b1 = 0.9f, b2 = 0.999f;
+            const float c1 = 1.0f - std::pow(b1, (float)s->adam_t), c2 = 1.0f - std::pow(b2, (float)s->adam_t);
+            adam_kernel<<<blocks_for(s->nparam), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->nparam,
+                                                               lr, b1, b2, 1e-10f, c1, c2);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess && step == steps - 1) {
+            e = cudaMemcpyAsync(&loss_h, s->dacc, sizeof(double), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    }
+    if (e == cudaSuccess) {
+        refresh_inference(s, st);
+        e = cudaStreamSynchronize(st);
+    }
+    if (last_loss) *last_loss = (float)loss_h;
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate training");
+}
+
+}  // extern "C"

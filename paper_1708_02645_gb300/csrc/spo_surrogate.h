@@ -1,0 +1,45 @@
+// Internal declarations of the learned surrogate shared by its host code and
+// its tensor-core perceptron.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spo_detail {
+
+constexpr int kSurrMaxLevels = 32;
+constexpr int kSurrMaxMats = 8;   // weight matrices (hidden layers + output)
+
+// Level geometry of the hashed grid, passed by value to the kernels.
+struct SurrLevels {
+    int levels = 0, features = 0;
+    int table = 0;          // entries per level (a power of two)
+    uint32_t mask = 0;      // table - 1
+    int R[kSurrMaxLevels] = {};
+    int dense[kSurrMaxLevels] = {};   // R^3 <= table: direct indexing
+};
+
+// The inference copy of the perceptron: BF16 weights W[l] ([out][in], row
+// major), FP32 biases b[l] ([out]).
+struct SurrMlpView {
+    int nl = 0;
+    int widths[kSurrMaxMats + 1] = {};
+    const __nv_bfloat16 *W[kSurrMaxMats] = {};
+    const float *b[kSurrMaxMats] = {};
+};
+
+// True when the fused tensor-core kernel serves this network: 2 features per
+// level, 16..64 encoded features (a multiple of 16), hidden layers of 128,
+// 1..3 hidden layers, N a multiple of 16 up to 384.
+bool surrogate_tc_supported(const SurrMlpView &v, const SurrLevels &lv);
+
+// Fused inference on the tcgen05 tensor cores: encoding of pos [P][3] with
+// the FP16 grid ([levels][table][2]), BF16 layer inputs, FP32 accumulation;
+// out is [P][5][N] FP32, or [P][N] (value rows) when values_only.
+cudaError_t surrogate_fused_tc(const SurrMlpView &v, const __half *grid, const SurrLevels &lv,
+                               const float *pos, int64_t P, float *out, bool values_only, int num_sms,
+                               cudaStream_t stream);
+
+}  // namespace spo_detail

@@ -56,6 +56,15 @@ SIGNATURES = [
     ("spo_get_param", _INT, [_P, _INT, ctypes.POINTER(_I64)]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
+    ("spo_surrogate_create", _INT, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    ("spo_surrogate_train", _INT, [_P, _P, _I64, _I64, ctypes.c_float, _P, ctypes.c_uint64, _P,
+                                   ctypes.POINTER(ctypes.c_float)]),
+    ("spo_surrogate_eval", _INT, [_P, _INT, _P, _I64, _P, _INT, _P]),
+    ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_float), _P, _P, _P,
+                                  _P]),
+    ("spo_surrogate_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    ("spo_surrogate_params", _INT, [_P, _P, _P, _P, _INT]),
+    ("spo_surrogate_destroy", _INT, [_P]),
     ("spo_rows", _INT, [_INT]),
     ("spo_status_str", ctypes.c_char_p, [_INT]),
     ("spo_last_error", ctypes.c_char_p, []),
@@ -419,6 +428,130 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) is not None:
             _check(load().spo_batch_destroy(self._h), "spo_batch_destroy")
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class _SurrogateSpec(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("log2_table", ctypes.c_int32),
+                ("features", ctypes.c_int32), ("r_min", ctypes.c_int32), ("r_max", ctypes.c_int32),
+                ("hidden", ctypes.c_int32), ("layers", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("N", ctypes.c_int64)]
+
+
+class Surrogate:
+    """Learned surrogate of an orbital set (hashed grid + softplus
+    perceptron) on the current CUDA device.
+
+    spec: any object with the fields levels, log2_table, features, r_min,
+    r_max, hidden, layers, N.  eval() gives V [P, N] or VGL [P, 5, N];
+    precision 0 evaluates the FP32 master parameters, 1 the FP16-grid /
+    BF16-weight inference copy."""
+
+    def __init__(self, spec, seed: int = 0):
+        self.spec = spec
+        c = _SurrogateSpec(int(spec.levels), int(spec.log2_table), int(spec.features),
+                           int(spec.r_min), int(spec.r_max), int(spec.hidden), int(spec.layers), 0,
+                           int(spec.N))
+        h = ctypes.c_void_p()
+        _check(load().spo_surrogate_create(ctypes.byref(c), int(seed), ctypes.byref(h)),
+               "spo_surrogate_create")
+        self._h = h
+        self.widths = [spec.levels * spec.features] + [spec.hidden] * spec.layers + [spec.N]
+
+    def _param_buffers(self):
+        T = 1 << self.spec.log2_table
+        grid = np.zeros((self.spec.levels, T, self.spec.features), dtype=np.float32)
+        W = [np.zeros((o, i), dtype=np.float32) for i, o in zip(self.widths[:-1], self.widths[1:])]
+        b = [np.zeros(o, dtype=np.float32) for o in self.widths[1:]]
+        return grid, W, b
+
+    def _params_call(self, grid, W, b, to_device):
+        Wp = (ctypes.c_void_p * len(W))(*[w.ctypes.data for w in W])
+        bp = (ctypes.c_void_p * len(b))(*[v.ctypes.data for v in b])
+        _check(load().spo_surrogate_params(self._h, grid.ctypes.data, Wp, bp, int(to_device)),
+               "spo_surrogate_params")
+
+    def set_params(self, grid, W, b):
+        """Load FP32 master parameters (grid [levels, T, F], W[l] [out, in], b[l] [out])."""
+        g0, W0, b0 = self._param_buffers()
+        grid = np.ascontiguousarray(np.asarray(grid, dtype=np.float32).reshape(g0.shape))
+        W = [np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(w0.shape)) for w, w0 in zip(W, W0)]
+        b = [np.ascontiguousarray(np.asarray(v, dtype=np.float32).reshape(v0.shape)) for v, v0 in zip(b, b0)]
+        if len(W) != len(W0) or len(b) != len(b0):
+            raise ValueError("wrong number of layers")
+        self._params_call(grid, W, b, True)
+
+    def get_params(self):
+        grid, W, b = self._param_buffers()
+        self._params_call(grid, W, b, False)
+        return grid, W, b
+
+    def train(self, teacher: "OrbitalSet", steps: int, batch: int, lr: float, channel_weights=None,
+              seed: int = 0, stream=None) -> float:
+        """Adam steps on teacher VGL targets; returns the last step's loss."""
+        cw = None
+        if channel_weights is not None:
+            cw = (ctypes.c_float * 5)(*[float(x) for x in channel_weights])
+        loss = ctypes.c_float()
+        _check(load().spo_surrogate_train(self._h, teacher.handle, int(steps), int(batch), float(lr),
+                                          cw, int(seed), _stream_handle(stream), ctypes.byref(loss)),
+               "spo_surrogate_train")
+        return float(loss.value)
+
+    def grad(self, pos, target, channel_weights=None, stream=None):
+        """Loss and FP32 gradients (grid, W list, b list) for device positions
+        [P, 3] and device targets [P, 5, N]; the parameters are unchanged."""
+        torch = _torch()
+        for t in (pos, target):
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("pos and target must be contiguous CUDA float32 tensors")
+        grid, W, b = self._param_buffers()
+        Wp = (ctypes.c_void_p * len(W))(*[w.ctypes.data for w in W])
+        bp = (ctypes.c_void_p * len(b))(*[v.ctypes.data for v in b])
+        cw = None
+        if channel_weights is not None:
+            cw = (ctypes.c_float * 5)(*[float(x) for x in channel_weights])
+        loss = ctypes.c_float()
+        _check(load().spo_surrogate_grad(self._h, ctypes.c_void_p(pos.data_ptr()),
+                                         ctypes.c_void_p(target.data_ptr()), int(pos.shape[0]), cw,
+                                         ctypes.byref(loss), grid.ctypes.data, Wp, bp,
+                                         _stream_handle(stream)), "spo_surrogate_grad")
+        return float(loss.value), grid, W, b
+
+    def eval(self, pos, out=None, kind="vgl", precision: int = 1, stream=None):
+        torch = _torch()
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        if pos.dtype != torch.float32 or not pos.is_cuda or not pos.is_contiguous():
+            raise TypeError("pos must be a contiguous CUDA float32 tensor [P, 3]")
+        P = pos.shape[0]
+        shape = (P, self.spec.N) if k == KIND_V else (P, 5, self.spec.N)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=pos.device)
+        _check(load().spo_surrogate_eval(self._h, k, ctypes.c_void_p(pos.data_ptr()), int(P),
+                                         ctypes.c_void_p(out.data_ptr()), int(precision),
+                                         _stream_handle(stream)), "spo_surrogate_eval")
+        return out
+
+    def footprint(self) -> int:
+        n = ctypes.c_size_t()
+        _check(load().spo_surrogate_footprint(self._h, ctypes.byref(n)), "spo_surrogate_footprint")
+        return int(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _check(load().spo_surrogate_destroy(self._h), "spo_surrogate_destroy")
             self._h = None
 
     def __del__(self):

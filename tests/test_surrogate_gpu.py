@@ -1,0 +1,174 @@
+"""GPU surrogate (spo_surrogate_*) against the FP64 reference oracle/surrogate.py.
+
+Tolerances, per output channel c, relative to max |ref_c| over the batch:
+* FP32 master path: 2e-4.  The sums are at most K = 128 terms long (the
+  encode adds 8 corners), so the FP32 error is below K u sum|terms| with
+  u = 2^-24 and sum|terms| a few times max|out_c|: about 1e-5; the margin
+  covers the cancelling Laplacian sums of the finest levels.
+* inference path (FP16 grid, BF16 weights and layer inputs): 4e-3 against
+  the reference's quantised reading.  Both round the same layer inputs to
+  bfloat16; an FP32 accumulation difference can flip one rounding by one
+  bfloat16 step (2^-8 relative) in a handful of activations.
+* gradients: 1e-3 of max |ref| per parameter array (FP32 sums of up to 5P
+  terms in atomic order).
+"""
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+from paper_1708_02645_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# ragged shapes: two dense and two hashed levels, widths that are not
+# multiples of the GEMM tiles
+RAGGED = S.SurrogateSpec(levels=4, log2_table=10, features=2, r_min=4, r_max=40, hidden=80,
+                         layers=2, N=72)
+# the full-size surrogate of the 384-orbital set (fused tensor-core inference)
+FULL = S.SurrogateSpec()
+# also served by the fused tensor-core kernel: one and two hidden layers, 16
+# and 48 encoded features, output chunks of 128 + 128 + 16 and of 48
+TC_ONE = S.SurrogateSpec(levels=8, log2_table=12, features=2, r_min=4, r_max=64, hidden=128,
+                         layers=1, N=48)
+TC_TWO = S.SurrogateSpec(levels=24, log2_table=14, features=2, r_min=4, r_max=128, hidden=128,
+                         layers=2, N=272)
+
+
+def torch():
+    import torch as t
+    return t
+
+
+def load(spo_lib, spec, params):
+    s = spo_lib.Surrogate(spec, seed=0)
+    s.set_params(params.grid, params.W, params.b)
+    return s
+
+
+def channel_errors(got, ref):
+    return [np.abs(got[:, c] - ref[:, c]).max() / max(np.abs(ref[:, c]).max(), 1e-30) for c in range(5)]
+
+
+@pytest.mark.parametrize("spec,P,grid_scale", [(RAGGED, 333, 0.5), (FULL, 96, 0.05)])
+def test_fp32_forward_matches_reference(spo_lib, spec, P, grid_scale):
+    t = torch()
+    p = S.as_float32(S.init_params(spec, seed=11, grid_scale=grid_scale))
+    pos = np.concatenate([inputs.uniform_positions(P - 20, 12), inputs.wide_positions(20, 13)])
+    ref, _ = S.forward(p, pos.astype(np.float64))
+    with load(spo_lib, spec, p) as s:
+        got = s.eval(t.from_numpy(pos).cuda(), precision=0).cpu().numpy().astype(np.float64)
+        v = s.eval(t.from_numpy(pos).cuda(), kind="v", precision=0).cpu().numpy()
+    err = channel_errors(got, ref)
+    assert max(err) < 2e-4, err
+    assert np.array_equal(v, got[:, 0].astype(np.float32))
+
+
+@pytest.mark.parametrize("spec,P,grid_scale", [(RAGGED, 333, 0.5), (FULL, 96, 0.05),
+                                               (FULL, 3001, 0.05), (TC_ONE, 333, 0.5),
+                                               (TC_TWO, 250, 0.3)])
+def test_inference_forward_matches_quantised_reference(spo_lib, spec, P, grid_scale):
+    t = torch()
+    p = S.as_float32(S.init_params(spec, seed=14, grid_scale=grid_scale))
+    pos = np.concatenate([inputs.uniform_positions(P - 10, 15), inputs.wide_positions(10, 16)])
+    ref, _ = S.forward(S.quantised(p), pos.astype(np.float64), act_round=S.round_bf16)
+    with load(spo_lib, spec, p) as s:
+        got = s.eval(t.from_numpy(pos).cuda(), precision=1).cpu().numpy().astype(np.float64)
+        v = s.eval(t.from_numpy(pos).cuda(), kind="v", precision=1).cpu().numpy()
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    err = channel_errors(got, ref)
+    assert max(err) < 4e-3, err
+    assert np.array_equal(v, got[:, 0].astype(np.float32))
+
+
+@pytest.mark.parametrize("given", [True, False])
+def test_gradients_match_reference(spo_lib, given):
+    t = torch()
+    spec = RAGGED
+    p = S.as_float32(S.init_params(spec, seed=16, grid_scale=0.5))
+    P = 257
+    pos = inputs.uniform_positions(P, 17)
+    target = inputs.normal(18, P * 5 * spec.N).reshape(P, 5, spec.N).astype(np.float32)
+    tg = target.astype(np.float64)
+    wch = [1.0, 0.25, 0.25, 0.25, 0.01] if given else \
+        [1.0 / np.mean(tg[:, c] ** 2) for c in range(5)]
+    L, gg, gW, gb = S.grads(p, pos.astype(np.float64), tg, wch)
+    with load(spo_lib, spec, p) as s:
+        loss, ggot, Wgot, bgot = s.grad(t.from_numpy(pos).cuda(), t.from_numpy(target).cuda(),
+                                        channel_weights=wch if given else None)
+        # the parameters are left as they were
+        g2, W2, b2 = s.get_params()
+        assert np.array_equal(g2, p.grid.astype(np.float32))
+    assert abs(loss - L) < 1e-5 * abs(L)
+    pairs = [(ggot, gg)] + list(zip(Wgot, gW)) + list(zip(bgot, gb))
+    for got, ref in pairs:
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 1e-3, err
+
+
+def test_params_round_trip_and_footprint(spo_lib):
+    spec = RAGGED
+    p = S.init_params(spec, seed=19, grid_scale=0.5)
+    with load(spo_lib, spec, p) as s:
+        g, W, b = s.get_params()
+        assert np.array_equal(g, p.grid.astype(np.float32))
+        for a, r in zip(W + b, p.W + p.b):
+            assert np.array_equal(a, r.astype(np.float32))
+        T = 1 << spec.log2_table
+        widths = spec.widths()
+        nw = sum(i * o for i, o in zip(widths[:-1], widths[1:]))
+        assert s.footprint() == 2 * spec.levels * T * spec.features + 2 * nw + 4 * sum(widths[1:])
+    with spo_lib.Surrogate(FULL, seed=0) as s:
+        # FP16 grid 32 MiB + BF16 weights + FP32 biases: about 33.9 MB
+        assert s.footprint() < 34_000_000
+
+
+def test_errors_and_empty(spo_lib):
+    t = torch()
+    with spo_lib.Surrogate(RAGGED, seed=0) as s:
+        pos = t.zeros((0, 3), device="cuda")
+        assert s.eval(pos).shape == (0, 5, RAGGED.N)
+        pos = t.rand((4, 3), device="cuda")
+        with pytest.raises(spo_lib.SpoError, match="SPO_EUNSUPPORTED"):
+            s.eval(pos, kind="vgh")
+        with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
+            s.eval(pos, precision=2)
+    bad = S.SurrogateSpec(levels=0)
+    with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
+        spo_lib.Surrogate(bad)
+
+
+def test_training_fits_the_spline(spo_lib):
+    """Adam on spline VGL targets lowers the loss by an order of magnitude;
+    the error of the trained surrogate against the spline is measured on
+    held-out positions (reported, and bounded loosely)."""
+    t = torch()
+    N = 16
+    coefs = inputs.plane_wave_coefs(16, 16, 16, N, seed=20, kmax=2.0).astype(np.float32)
+    spec = S.SurrogateSpec(levels=8, log2_table=14, features=2, r_min=4, r_max=64, hidden=64,
+                           layers=2, N=N)
+    with spo_lib.OrbitalSet(coefs) as teacher, spo_lib.Surrogate(spec, seed=21) as s:
+        first = s.train(teacher, steps=1, batch=4096, lr=1e-2, seed=22)
+        last = s.train(teacher, steps=400, batch=4096, lr=1e-2, seed=23)
+        assert last < 0.1 * first, (first, last)
+        pos = t.from_numpy(inputs.uniform_positions(5000, 24)).cuda()
+        want = teacher.eval(pos, kind="vgl").cpu().numpy()
+        for prec in (0, 1):
+            got = s.eval(pos, precision=prec).cpu().numpy()
+            rel = [np.sqrt(np.mean((got[:, c] - want[:, c]) ** 2) / np.mean(want[:, c] ** 2))
+                   for c in range(5)]
+            print(f"precision {prec}: relative RMS error V {rel[0]:.3g} G {max(rel[1:4]):.3g} "
+                  f"L {rel[4]:.3g}")
+            assert rel[0] < 0.3, rel
+
+
+def test_initial_parameters_follow_the_generator_definition(spo_lib):
+    """spo_surrogate_create draws the same splitmix64 streams as the
+    reference's init_params (grid U(-1e-4, 1e-4), weights U(+-1/sqrt(in)),
+    biases 0), rounded once to FP32."""
+    ref = S.as_float32(S.init_params(RAGGED, seed=25))
+    with spo_lib.Surrogate(RAGGED, seed=25) as s:
+        g, W, b = s.get_params()
+    assert np.array_equal(g, ref.grid.astype(np.float32))
+    for a, r in zip(W + b, ref.W + ref.b):
+        assert np.array_equal(a, r.astype(np.float32))

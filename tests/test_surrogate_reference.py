@@ -99,3 +99,38 @@ def test_c2_across_cell_faces():
     a, _ = S.forward(p, base - e)
     b, _ = S.forward(p, base + e)
     assert np.abs(a - b).max() < 1e-6
+
+
+def test_rounding_helpers_match_library_conversions():
+    """round_bf16 / round_fp16 agree with torch's bfloat16 and numpy's
+    float16 conversions (round to nearest even) on FP32 inputs, including
+    ties, subnormals of binary16 and large magnitudes."""
+    torch = pytest.importorskip("torch")
+    x = np.concatenate([
+        (inputs.normal(7, 4000) * 10.0 ** (inputs.uniform01(8, 4000) * 12 - 6)),
+        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 3e-6, -7e-7, 65504.0, 0.0]),
+    ]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(S.round_bf16(x.astype(np.float64)), want)
+    assert S.round_bf16(1.0 + 2.0 ** -8) == 1.0          # tie to even
+    assert S.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    xh = x[np.abs(x) <= 65504.0]
+    half = xh.astype(np.float16).astype(np.float64)
+    assert np.array_equal(S.round_fp16(xh.astype(np.float64)), half)
+
+
+def test_quantised_forward_is_close_and_rounds_inputs():
+    """The inference reading (FP16 grid, BF16 weights, BF16 layer inputs)
+    stays within a few bfloat16 roundings of the exact function, and with
+    the identity as act_round and unquantised parameters it is the exact
+    function bit for bit."""
+    p = small_params(seed=5)
+    pos = inputs.uniform_positions(50, 9).astype(np.float64)
+    exact, _ = S.forward(p, pos)
+    same, _ = S.forward(p, pos, act_round=lambda h: h)
+    assert np.array_equal(exact, same)
+    q, _ = S.forward(S.quantised(p), pos, act_round=S.round_bf16)
+    for c in range(5):
+        scale = np.abs(exact[:, c]).max()
+        assert np.abs(q[:, c] - exact[:, c]).max() < 0.05 * scale
+        assert np.abs(q[:, c] - exact[:, c]).max() > 0.0
