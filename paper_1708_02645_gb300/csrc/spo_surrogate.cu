@@ -384,6 +384,8 @@ struct spo_surrogate {
 
     bool use_tc = false;   // the fused tensor-core kernel serves precision 1
     int num_sms = 0;
+    spo_detail::SurrImagePlan plan{};   // its weight image
+    uint8_t *wimg = nullptr;
 };
 
 namespace {
@@ -461,12 +463,26 @@ cudaError_t forward_fp32(spo_surrogate *s, const float *pos, int64_t P, float *o
     return cudaSuccess;
 }
 
+spo_detail::SurrMlpView mlp_view(const spo_surrogate *s) {
+    spo_detail::SurrMlpView v;
+    v.nl = s->nl;
+    for (int l = 0; l <= s->nl; ++l) v.widths[l] = s->widths[l];
+    for (int l = 0; l < s->nl; ++l) {
+        v.W[l] = s->w16 + s->w16_off[l];
+        v.b[l] = s->param + s->b_off[l];
+    }
+    return v;
+}
+
+// FP16 grid, BF16 weights and (for the fused kernel) the weight image from
+// the FP32 master parameters.
 void refresh_inference(spo_surrogate *s, cudaStream_t st) {
     to_half_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grid16, s->grid_n);
     for (int l = 0; l < s->nl; ++l) {
         const int64_t n = (int64_t)s->widths[l] * s->widths[l + 1];
         to_bf16_kernel<<<blocks_for(n), 256, 0, st>>>(s->param + s->w_off[l], s->w16 + s->w16_off[l], n);
     }
+    if (s->use_tc) spo_detail::surrogate_write_image(mlp_view(s), s->plan, s->wimg, st);
 }
 
 // Channel weights of the loss: given, else 1 / mean(target_c^2) of `target`.
@@ -580,16 +596,6 @@ cudaError_t surrogate_forward_inference(spo_surrogate *s, const float *pos, int6
     return cudaSuccess;
 }
 
-SurrMlpView mlp_view(const spo_surrogate *s) {
-    SurrMlpView v;
-    v.nl = s->nl;
-    for (int l = 0; l <= s->nl; ++l) v.widths[l] = s->widths[l];
-    for (int l = 0; l < s->nl; ++l) {
-        v.W[l] = s->w16 + s->w16_off[l];
-        v.b[l] = s->param + s->b_off[l];
-    }
-    return v;
-}
 
 }  // namespace spo_detail
 
@@ -651,10 +657,17 @@ spo_status spo_surrogate_create(const spo_surrogate_spec *spec, uint64_t seed, s
     if (e == cudaSuccess) e = cudaMalloc(&s->grid16, sizeof(__half) * s->grid_n);
     if (e == cudaSuccess) e = cudaMalloc(&s->w16, sizeof(__nv_bfloat16) * w16);
     if (e == cudaSuccess) e = cudaMalloc(&s->dacc, sizeof(double) * 8);
+    if (e == cudaSuccess && s->use_tc) {
+        spo_detail::SurrMlpView v;
+        v.nl = s->nl;
+        for (int l = 0; l <= s->nl; ++l) v.widths[l] = s->widths[l];
+        s->plan = spo_detail::surrogate_image_plan(v);
+        e = cudaMalloc(&s->wimg, s->plan.total);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
-        cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc);
+        cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
         delete s;
         return fail(SPO_ENOMEM, "surrogate parameter allocation failed");
     }
@@ -686,7 +699,7 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     cudaDeviceSynchronize();
     free_scratch(s);
     cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
-    cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc);
+    cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
     delete s;
     return SPO_OK;
 }
@@ -734,8 +747,8 @@ spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos,
     DeviceGuard guard(s->device);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (precision == 1 && s->use_tc) {   // one fused launch, no scratch
-        const cudaError_t e = spo_detail::surrogate_fused_tc(spo_detail::mlp_view(s), s->grid16, s->lv, pos, P,
-                                                             out, kind == SPO_KIND_V, s->num_sms, st);
+        const cudaError_t e = spo_detail::surrogate_fused_tc(mlp_view(s), s->wimg, s->plan, s->grid16, s->lv, pos,
+                                                             P, out, kind == SPO_KIND_V, s->num_sms, st);
         return e == cudaSuccess ? SPO_OK : cuda_fail(e, "fused surrogate evaluation");
     }
     // evaluate in chunks of at most 65536 positions (bounded scratch)

@@ -30,16 +30,36 @@ struct SurrMlpView {
     const float *b[kSurrMaxMats] = {};
 };
 
+// The fused kernel streams the weights from an image in global memory: one
+// block per hidden layer (128 rows in the 128-byte swizzle layout, one
+// K-block for the first layer, two for the others) and one per chunk of
+// kSurrOutChunk output rows (two K-blocks), in the order the kernel uses
+// them.
+constexpr int kSurrOutChunk = 96;
+constexpr int kSurrMaxLoads = 8;
+
+struct SurrImagePlan {
+    uint32_t off[kSurrMaxLoads] = {}, bytes[kSurrMaxLoads] = {};
+    int nloads = 0;
+    uint32_t total = 0;
+};
+
 // True when the fused tensor-core kernel serves this network: 2 features per
 // level, 16..64 encoded features (a multiple of 16), hidden layers of 128,
 // 1..3 hidden layers, N a multiple of 16 up to 384.
 bool surrogate_tc_supported(const SurrMlpView &v, const SurrLevels &lv);
 
+SurrImagePlan surrogate_image_plan(const SurrMlpView &v);
+
+// Writes the weight image of v (BF16 weights) into img (plan.total bytes).
+cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &plan, uint8_t *img,
+                                  cudaStream_t stream);
+
 // Fused inference on the tcgen05 tensor cores: encoding of pos [P][3] with
 // the FP16 grid ([levels][table][2]), BF16 layer inputs, FP32 accumulation;
-// out is [P][5][N] FP32, or [P][N] (value rows) when values_only.
-cudaError_t surrogate_fused_tc(const SurrMlpView &v, const __half *grid, const SurrLevels &lv,
-                               const float *pos, int64_t P, float *out, bool values_only, int num_sms,
-                               cudaStream_t stream);
+// out is [P][5][N] FP32, or [P][N] (value channel only) when values_only.
+cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const SurrImagePlan &plan,
+                               const __half *grid, const SurrLevels &lv, const float *pos, int64_t P,
+                               float *out, bool values_only, int num_sms, cudaStream_t stream);
 
 }  // namespace spo_detail

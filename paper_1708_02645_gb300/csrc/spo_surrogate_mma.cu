@@ -3,28 +3,33 @@
 // accumulation in tensor memory) with the value / gradient / Laplacian
 // channels, in one persistent kernel.
 //
-// Tile: 128 MMA rows = 4 lane quarters x (6 positions x 5 channels + 2 pad
-// rows), i.e. 24 positions.  Row 32 q + 5 i + c holds channel c of position
-// 6 q + i of the tile, so a position's five channels sit in five adjacent
-// lanes of one warp and the softplus jets exchange them with shuffles.
-// Every linear layer is one GEMM over the 128 rows: D[128 x n] = A[128 x k]
-// W^T, A from shared memory (BF16, 128-byte swizzle), W resident in shared
-// memory for the kernel's lifetime, D in tensor memory.  The epilogue of a
-// hidden layer reads D (tcgen05.ld), adds the bias to the value rows,
-// applies h = sp(z0), h_d = sp'(z0) z_d, h_L = sp''(z0) |z_d|^2 + sp'(z0) z_L
-// and writes BF16 A for the next layer; the output layer's epilogue adds the
-// bias and stores FP32 rows [P][5][N] (or the value rows only, [P][N]).
+// A tile is 128 positions, one per MMA row (tensor-memory lane).  Channel c
+// of the activations is its own BF16 A operand H[c] [128 rows][128 K] in
+// shared memory (128-byte swizzle), and every linear layer is one MMA group
+// per channel, D_c[128 x n] = H[c] W^T, into its own tensor-memory column
+// block.  A hidden layer runs in two phases so that five 128-column blocks
+// never have to coexist in the 512 columns:
+//   1. D_0..D_3 (value, gradient) into columns 0..511; the epilogue adds the
+//      bias to D_0 and writes h0 = sp(z0), h_d = sp'(z0) z_d over H[0..3]
+//      (already consumed), and parks T = sp''(z0) |z_d|^2 and sp'(z0) in
+//      columns 128..383;
+//   2. D_4 (Laplacian) into columns 0..127 from H[4]; the epilogue writes
+//      h_L = T + sp'(z0) z_L over H[4].
+// The output layer runs in chunks of 96 columns (5 x 96 <= 512), each chunk
+// storing FP32 [P][5][N] rows (bias on the value channel).  Value-only
+// evaluation carries channel 0 alone.
 //
-// Shared memory: A0 (encoded features, one 64-column K-block) 16 KB, AH
-// (hidden activations, two K-blocks) 32 KB, W0 16 KB, one 32 KB block per
-// hidden-to-hidden layer, the output layer N x 256 bytes: 224 KB for the
-// 32-128-128-128-384 network.  Tensor memory: 512 columns (the output layer
-// needs N <= 384).
+// Weights do not stay resident (H takes 160 KB): one thread streams them
+// from an image pre-swizzled in global memory (one block per layer or output
+// chunk, L2-resident) into two 32 KB stages with bulk copies, prefetching
+// the next block while the current one is used.  The encoded features are
+// written into K-block 0 of H[c] (the first layer's A operand).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "spo_batch.h"
 #include "spo_surrogate.h"
@@ -36,12 +41,18 @@ namespace {
 
 using namespace spo_dev;
 using spo_detail::SurrLevels;
+using spo_detail::kSurrMaxLoads;
 
-constexpr int kThreads = 256;        // 8 warps: two per lane quarter
-constexpr int kPosPerQuarter = 6;
-constexpr int kTilePos = 4 * kPosPerQuarter;
+constexpr int kThreads = 512;        // 16 warps: 4 per tensor-memory lane quarter
+constexpr int kTile = 128;           // positions per tile (MMA rows)
 constexpr int kHidden = 128;
-constexpr uint32_t kBlock = 128 * 128;   // one K-block of 128 rows x 64 BF16
+constexpr int kChunk = spo_detail::kSurrOutChunk;   // output columns per chunk
+constexpr uint32_t kBlock = 128 * 128;              // K-block: 128 rows x 64 BF16
+constexpr uint32_t kChan = 2 * kBlock;              // one channel of H (K = 128)
+constexpr uint32_t kStage = 2 * kBlock;             // one weight stage
+constexpr uint32_t kOffStage = 5 * kChan;
+constexpr uint32_t kOffBar = kOffStage + 2 * kStage;   // full[2], mma, tmem slot
+constexpr uint32_t kSmemBytes = kOffBar + 64 + 1024;   // + alignment slack
 constexpr uint32_t kTmemCols = 512;
 
 struct FusedArgs {
@@ -49,48 +60,29 @@ struct FusedArgs {
     SurrLevels lv;
     const float *pos;
     int64_t P;
-    const __nv_bfloat16 *W[spo_detail::kSurrMaxMats];
+    const uint8_t *wimg;   // weight image: one block per load
+    uint32_t load_off[kSurrMaxLoads], load_bytes[kSurrMaxLoads];
+    int nloads;
     const float *b[spo_detail::kSurrMaxMats];
     int nl;                // weight matrices (2..4)
-    int K0;                // encoded features (16, 32, 48 or 64)
+    int K0;                // encoded features (16..64, multiple of 16)
     int N;                 // outputs (multiple of 16, <= 384)
-    int values_only;       // store the value rows only ([P][N])
+    int nch;               // channels carried: 5 (VGL) or 1 (V)
+    int tile_pos;          // positions per tile (<= 128; the remaining MMA rows idle)
     float *out;
     unsigned int *status;
 };
 
-struct Layout {
-    uint32_t a0, ah, w0, wh, wl, bar, slot, bytes;
-};
-
-__host__ __device__ inline Layout layout_of(int nl, int N) {
-    Layout L;
-    L.a0 = 0;
-    L.ah = L.a0 + kBlock;
-    L.w0 = L.ah + 2 * kBlock;
-    L.wh = L.w0 + kBlock;                               // hidden-to-hidden layers 1 .. nl-2
-    L.wl = L.wh + (uint32_t)(nl - 2) * 2 * kBlock;      // output layer: two K-blocks of N rows
-    L.bar = L.wl + (uint32_t)N * 256;
-    L.slot = L.bar + 8;
-    L.bytes = L.bar + 16;
-    return L;
-}
-
-// Copies W [n][k] (row major, BF16) into K-blocks of the 128-byte swizzle
-// layout: block kb holds columns 64 kb .. 64 kb + 63 of all n rows.
-__device__ void stage_weights(uint8_t *dst, const __nv_bfloat16 *W, int n, int k) {
-    const int chunks = k / 8;
-    for (int i = threadIdx.x; i < n * chunks; i += kThreads) {
-        const int r = i / chunks, kc = i - r * chunks;
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(W + (size_t)r * k) + kc);
-        const int kb = kc >> 3;
-        *reinterpret_cast<uint4 *>(dst + (uint32_t)kb * (uint32_t)n * 128u + sw128_offset(r, (kc & 7) * 8)) = v;
-    }
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// 8 floats (32 bytes, 32-byte aligned) streamed to global memory.
+__device__ __forceinline__ void store8_cs(float *p, const float *v) {
+    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+                 "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ void softplus_jet(float z, float &sp, float &d1, float &d2) {
@@ -101,48 +93,67 @@ __device__ __forceinline__ void softplus_jet(float z, float &sp, float &d1, floa
     d2 = d1 * (1.0f - d1);
 }
 
-// Encoded features of the tile's positions into A0 (BF16, rows as above).
-__device__ void encode_tile(const FusedArgs &a, uint8_t *a0, int64_t tile) {
-    const int L = a.lv.levels;
-    for (int item = threadIdx.x; item < kTilePos * L; item += kThreads) {
-        const int pi = item / L, l = item - pi * L;
-        const int64_t p = tile * kTilePos + pi;
-        float acc[5][2] = {};
-        if (p < a.P) {
-            const float r[3] = {__ldg(a.pos + 3 * p), __ldg(a.pos + 3 * p + 1), __ldg(a.pos + 3 * p + 2)};
-            uint32_t slot[8];
-            float cw[5][8];
-            level_corners(r, a.lv.R[l], a.lv.dense[l] != 0, a.lv.mask, slot, cw);
-            const __half2 *g = a.grid + (size_t)l * a.lv.table;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 th = __half22float2(g[slot[q]]);
-#pragma unroll
-                for (int ch = 0; ch < 5; ++ch) {
-                    acc[ch][0] = fmaf(cw[ch][q], th.x, acc[ch][0]);
-                    acc[ch][1] = fmaf(cw[ch][q], th.y, acc[ch][1]);
-                }
-            }
-        }
-        const int row0 = 32 * (pi / kPosPerQuarter) + 5 * (pi % kPosPerQuarter);
-#pragma unroll
-        for (int ch = 0; ch < 5; ++ch)
-            *reinterpret_cast<uint32_t *>(a0 + sw128_offset(row0 + ch, 2 * l)) = pack_bf16(acc[ch][0], acc[ch][1]);
-    }
+// 8 BF16 (16 bytes) of row `row`, columns k .. k + 7 (k a multiple of 8) of
+// channel block ch.
+__device__ __forceinline__ void store_h8(uint8_t *H, int ch, int row, int k, const float (&h)[8]) {
+    uint8_t *blk = H + (uint32_t)ch * kChan + (uint32_t)(k >> 6) * kBlock;
+    *reinterpret_cast<uint4 *>(blk + sw128_offset(row, k & 63)) =
+        make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
 }
 
-// Issue one layer: D[128 x n] = A[128 x k] W^T from the K-blocks at a and w
-// (w: blocks of n_rows rows), output columns n0 .. n0 + n - 1 (chunks of at
-// most 128 columns).
-__device__ void issue_layer(uint32_t tmem, uint32_t a, uint32_t w, int k, int n_rows, int n0, int n) {
-    for (int c0 = 0; c0 < n; c0 += 128) {
-        const int nn = min(128, n - c0);
-        const uint32_t idesc = umma_idesc_bf16(128, nn);
-        for (int kk = 0; kk < k / 16; ++kk) {
-            const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
-            umma_bf16(tmem + (uint32_t)(n0 + c0), umma_desc_sw128(a + kb * kBlock + ko),
-                      umma_desc_sw128(w + kb * (uint32_t)n_rows * 128u + (uint32_t)(n0 + c0) * 128u + ko),
-                      idesc, kk > 0);
+// Encoded features of the tile's positions into K-block 0 of H[c], c < nch
+// (rows tile_pos .. 127 are not written: their MMA rows are never stored).
+// Items (row, level) go four per thread and pass: all 32 corner gathers of
+// a pass are issued before any is used.
+__device__ void encode_tile(const FusedArgs &a, uint8_t *H, int64_t tile) {
+    const int L = a.lv.levels;
+    const int nitems = a.tile_pos * L;
+    for (int base = threadIdx.x; base < nitems; base += 4 * kThreads) {
+        __half2 th[4][8];
+        float tt[4][3];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int item = base + k * kThreads;
+            const int row = item / L, l = item - row * L;
+            const int64_t p = tile * a.tile_pos + row;
+            if (item < nitems && p < a.P) {
+                int c[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) level_axis(__ldg(a.pos + 3 * p + d), a.lv.R[l], c[d], tt[k][d]);
+                uint32_t slot[8];
+                corner_slots(c, a.lv.R[l], a.lv.dense[l] != 0, a.lv.mask, slot);
+                const __half2 *g = a.grid + (size_t)l * a.lv.table;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) th[k][q] = g[slot[q]];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) th[k][q] = __float2half2_rn(0.0f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) tt[k][d] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int item = base + k * kThreads;
+            if (item >= nitems) break;
+            const int row = item / L, l = item - row * L;
+            float cw[5][8];
+            corner_weights(tt[k], a.lv.R[l], cw);
+            float acc[5][2] = {};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 v = __half22float2(th[k][q]);
+#pragma unroll
+                for (int ch = 0; ch < 5; ++ch) {
+                    acc[ch][0] = fmaf(cw[ch][q], v.x, acc[ch][0]);
+                    acc[ch][1] = fmaf(cw[ch][q], v.y, acc[ch][1]);
+                }
+            }
+#pragma unroll
+            for (int ch = 0; ch < 5; ++ch)
+                if (ch < a.nch)
+                    *reinterpret_cast<uint32_t *>(H + (uint32_t)ch * kChan + sw128_offset(row, 2 * l)) =
+                        pack_bf16(acc[ch][0], acc[ch][1]);
         }
     }
 }
@@ -150,136 +161,261 @@ __device__ void issue_layer(uint32_t tmem, uint32_t a, uint32_t w, int k, int n_
 __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __grid_constant__ FusedArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const Layout Lo = layout_of(a.nl, a.N);
+    uint8_t *H = sm;
     const uint32_t s0 = smem_addr(sm);
-    const uint32_t bar = s0 + Lo.bar;
+    const uint32_t sH = s0, sStage = s0 + kOffStage;
+    const uint32_t full_bar = s0 + kOffBar;   // two barriers, 8 bytes apart
+    const uint32_t mma_bar = s0 + kOffBar + 16;
+    const uint32_t slot = s0 + kOffBar + 24;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool leader = threadIdx.x == 0;
 
-    if (warp == 0) tmem_alloc(s0 + Lo.slot, kTmemCols);
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+    const int64_t ntiles = (a.P + a.tile_pos - 1) / a.tile_pos;
+    const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const uint64_t total_loads = (uint64_t)my_tiles * (uint64_t)a.nloads;
+    uint64_t issued = 0, consumed = 0;   // weight loads (leader only)
+
+    auto issue_load = [&](uint64_t g) {
+        const int i = (int)(g % (uint64_t)a.nloads);
+        const uint32_t bar = full_bar + 8u * (uint32_t)(g & 1);
+        mbar_arrive_expect_tx(bar, a.load_bytes[i]);
+        bulk_load(sStage + (uint32_t)(g & 1) * kStage, a.wimg + a.load_off[i], a.load_bytes[i], bar);
+    };
+
+    if (warp == 0) tmem_alloc(slot, kTmemCols);
+    if (leader) {
+        mbar_init(full_bar, 1);
+        mbar_init(full_bar + 8, 1);
+        mbar_init(mma_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // zero the activation blocks (pad rows and pad columns stay zero), stage the weights
-    for (uint32_t i = threadIdx.x; i < 3 * kBlock / 16; i += kThreads)
-        reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
-    stage_weights(sm + Lo.w0, a.W[0], kHidden, a.K0);
-    for (int l = 1; l < a.nl - 1; ++l) stage_weights(sm + Lo.wh + (uint32_t)(l - 1) * 2 * kBlock, a.W[l], kHidden, kHidden);
-    stage_weights(sm + Lo.wl, a.W[a.nl - 1], a.N, kHidden);
-    fence_proxy_async_smem();
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(sm + Lo.slot);
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(sm + kOffBar + 24);
+    if (leader)
+        while (issued < total_loads && issued < 2) issue_load(issued++);
 
-    const int wq = warp & 3, half = warp >> 2;
-    const int qi = lane / 5, ch = lane - 5 * qi;
-    const bool pad = lane >= 5 * kPosPerQuarter;
-    const int base = pad ? lane : 5 * qi;
+    const int wq = warp & 3, grp = warp >> 2;         // lane quarter, group within it
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * wq) << 16);
-    const int row = 32 * wq + lane;
-    uint32_t phase = 0;
+    const int row = 32 * wq + lane;                    // position within the tile
+    uint32_t mma_phase = 0;
     bool failed = false;
-    const int64_t ntiles = (a.P + kTilePos - 1) / kTilePos;
 
-    auto wait_mma = [&]() -> bool {
-        const bool ok = mbar_wait_bounded(bar, phase);
-        const bool bad = __syncthreads_or(!ok) != 0;
-        if (!bad) phase ^= 1u;
+    // Leader: wait for the weight block of load g (bounded).
+    auto weights_ready = [&](uint64_t g) -> bool {
+        return mbar_wait_bounded(full_bar + 8u * (uint32_t)(g & 1), (uint32_t)((g >> 1) & 1));
+    };
+    // All threads: wait for the MMA group just committed; a failure anywhere
+    // (including the leader's weight wait, `leader_bad`) is seen by all.
+    auto wait_mma = [&](bool leader_bad) -> bool {
+        const bool ok = mbar_wait_bounded(mma_bar, mma_phase);
+        const bool bad = __syncthreads_or(!ok || leader_bad) != 0;
+        mma_phase ^= 1u;
         tc_fence_after_sync();
         return !bad;
     };
+    // Leader: the stage of load g is free again; prefetch load g + 2 into it.
+    auto release = [&](uint64_t g) {
+        consumed = g + 1;
+        if (g + 2 < total_loads && issued == g + 2) issue_load(issued++);
+    };
 
-    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        encode_tile(a, sm + Lo.a0, tile);
+    int64_t it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
+        encode_tile(a, H, tile);
         fence_proxy_async_smem();
         tc_fence_before_sync();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after_sync();
-            issue_layer(tmem, s0 + Lo.a0, s0 + Lo.w0, a.K0, kHidden, 0, kHidden);
-            umma_commit(bar);
-        }
-        if (!wait_mma()) { failed = true; break; }
 
-        for (int l = 0; l < a.nl - 1; ++l) {
-            // epilogue of hidden layer l: softplus jets into AH
-            const float *bias = a.b[l];
-            for (int c16 = half; c16 < kHidden / 16; c16 += 2) {
-                float z[16];
-                tmem_ld16(lane_addr + (uint32_t)(c16 * 16), z);
-                uint32_t pk[8];
-#pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    float h[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const float zj = z[j + u] + (ch == 0 ? __ldg(bias + c16 * 16 + j + u) : 0.0f);
-                        const float z0 = __shfl_sync(0xffffffffu, zj, base);
-                        const float sq = zj * zj;
-                        const float s1 = __shfl_sync(0xffffffffu, sq, (base + 1) & 31);
-                        const float s2 = __shfl_sync(0xffffffffu, sq, (base + 2) & 31);
-                        const float s3 = __shfl_sync(0xffffffffu, sq, (base + 3) & 31);
-                        float sp, d1, d2;
-                        softplus_jet(z0, sp, d1, d2);
-                        h[u] = ch == 0 ? sp : (ch < 4 ? d1 * zj : fmaf(d2, s1 + s2 + s3, d1 * zj));
+        for (int l = 0; l < a.nl && !failed; ++l) {
+            const uint64_t g0 = (uint64_t)it * (uint64_t)a.nloads + (uint64_t)l;
+            if (l < a.nl - 1) {
+                // ---- hidden layer l: phase 1 (value and gradient channels)
+                const int K = l == 0 ? a.K0 : kHidden;
+                const uint32_t stage = sStage + (uint32_t)(g0 & 1) * kStage;
+                bool bad = false;
+                if (leader) {
+                    tc_fence_after_sync();
+                    bad = !weights_ready(g0);
+                    if (!bad) {
+                        for (int c = 0; c < min(a.nch, 4); ++c)
+                            for (int kk = 0; kk < K / 16; ++kk) {
+                                const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+                                umma_bf16(tmem + 128u * c, umma_desc_sw128(sH + c * kChan + kb * kBlock + ko),
+                                          umma_desc_sw128(stage + kb * kBlock + ko), umma_idesc_bf16(128, kHidden),
+                                          kk > 0);
+                            }
                     }
-                    pk[j / 2] = pack_bf16(h[0], h[1]);
+                    umma_commit(mma_bar);
                 }
-                if (!pad) {
-                    uint8_t *blk = sm + Lo.ah + (uint32_t)(c16 >> 2) * kBlock;
-                    const int k0 = (c16 & 3) * 16;
-                    *reinterpret_cast<uint4 *>(blk + sw128_offset(row, k0)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                    *reinterpret_cast<uint4 *>(blk + sw128_offset(row, k0 + 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-                }
-            }
-            fence_proxy_async_smem();
-            tc_fence_before_sync();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                tc_fence_after_sync();
-                if (l + 1 < a.nl - 1)
-                    issue_layer(tmem, s0 + Lo.ah, s0 + Lo.wh + (uint32_t)l * 2 * kBlock, kHidden, kHidden, 0, kHidden);
-                else
-                    issue_layer(tmem, s0 + Lo.ah, s0 + Lo.wl, kHidden, a.N, 0, a.N);
-                umma_commit(bar);
-            }
-            if (!wait_mma()) { failed = true; break; }
-        }
-        if (failed) break;
+                if (!wait_mma(bad)) { failed = true; break; }
+                if (a.nch == 1 && leader) release(g0);
 
-        // output epilogue: bias on the value rows, FP32 stores
-        const int64_t p = tile * kTilePos + kPosPerQuarter * wq + qi;
-        const bool store = !pad && p < a.P && (!a.values_only || ch == 0);
-        const float *bias = a.b[a.nl - 1];
-        float *dst = a.values_only ? a.out + p * a.N : a.out + (p * 5 + ch) * a.N;
-        for (int c16 = half; c16 < a.N / 16; c16 += 2) {
-            float z[16];
-            tmem_ld16(lane_addr + (uint32_t)(c16 * 16), z);
-            if (store) {
-                if (ch == 0) {
+                const float *bias = a.b[l];
+                for (int u = 0; u < 4; ++u) {
+                    const int j0 = 32 * grp + 8 * u;   // 8 units
+                    float z0[8], bb[8];
+                    tmem_ld8(lane_addr + (uint32_t)j0, z0);
+                    const float4 b0 = __ldg(reinterpret_cast<const float4 *>(bias + j0));
+                    const float4 b1 = __ldg(reinterpret_cast<const float4 *>(bias + j0 + 4));
+                    bb[0] = b0.x; bb[1] = b0.y; bb[2] = b0.z; bb[3] = b0.w;
+                    bb[4] = b1.x; bb[5] = b1.y; bb[6] = b1.z; bb[7] = b1.w;
+                    if (a.nch == 1) {
+                        float h[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) z[j] += __ldg(bias + c16 * 16 + j);
+                        for (int j = 0; j < 8; ++j) {
+                            float d1, d2;
+                            softplus_jet(z0[j] + bb[j], h[j], d1, d2);
+                        }
+                        store_h8(H, 0, row, j0, h);
+                    } else {
+                        float zx[8], zy[8], zz[8];
+                        tmem_ld8(lane_addr + 128u + (uint32_t)j0, zx);
+                        tmem_ld8(lane_addr + 256u + (uint32_t)j0, zy);
+                        tmem_ld8(lane_addr + 384u + (uint32_t)j0, zz);
+                        float h0[8], t[8], d1v[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float d2;
+                            softplus_jet(z0[j] + bb[j], h0[j], d1v[j], d2);
+                            t[j] = d2 * fmaf(zx[j], zx[j], fmaf(zy[j], zy[j], zz[j] * zz[j]));
+                            zx[j] *= d1v[j];
+                            zy[j] *= d1v[j];
+                            zz[j] *= d1v[j];
+                        }
+                        store_h8(H, 0, row, j0, h0);
+                        store_h8(H, 1, row, j0, zx);
+                        store_h8(H, 2, row, j0, zy);
+                        store_h8(H, 3, row, j0, zz);
+                        // park T and sp' in columns this thread has read (its own lane)
+                        tmem_st8(lane_addr + 128u + (uint32_t)j0, t);
+                        tmem_st8(lane_addr + 256u + (uint32_t)j0, d1v);
+                    }
                 }
-                float4 *d4 = reinterpret_cast<float4 *>(dst + c16 * 16);
+                if (a.nch == 5) tmem_wait_st();
+                fence_proxy_async_smem();
+                tc_fence_before_sync();
+                __syncthreads();
+
+                if (a.nch == 5) {
+                    // ---- phase 2 (Laplacian channel) into columns 0..127
+                    if (leader) {
+                        tc_fence_after_sync();
+                        for (int kk = 0; kk < K / 16; ++kk) {
+                            const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+                            umma_bf16(tmem, umma_desc_sw128(sH + 4 * kChan + kb * kBlock + ko),
+                                      umma_desc_sw128(stage + kb * kBlock + ko), umma_idesc_bf16(128, kHidden), kk > 0);
+                        }
+                        umma_commit(mma_bar);
+                    }
+                    if (!wait_mma(false)) { failed = true; break; }
+                    if (leader) release(g0);
+                    for (int u = 0; u < 4; ++u) {
+                        const int j0 = 32 * grp + 8 * u;
+                        float zl[8], t[8], d1v[8];
+                        tmem_ld8(lane_addr + (uint32_t)j0, zl);
+                        tmem_ld8(lane_addr + 128u + (uint32_t)j0, t);
+                        tmem_ld8(lane_addr + 256u + (uint32_t)j0, d1v);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) __stcs(d4 + j, make_float4(z[4 * j], z[4 * j + 1], z[4 * j + 2], z[4 * j + 3]));
+                        for (int j = 0; j < 8; ++j) zl[j] = fmaf(d1v[j], zl[j], t[j]);
+                        store_h8(H, 4, row, j0, zl);
+                    }
+                    fence_proxy_async_smem();
+                    tc_fence_before_sync();
+                    __syncthreads();
+                }
+            } else {
+                // ---- output layer, chunks of kChunk columns
+                const float *bias = a.b[l];
+                const int64_t p = row < a.tile_pos ? tile * a.tile_pos + row : a.P;
+                for (int n0 = 0, ci = 0; n0 < a.N; n0 += kChunk, ++ci) {
+                    const int nn = min(kChunk, a.N - n0);
+                    const uint64_t g = (uint64_t)it * (uint64_t)a.nloads + (uint64_t)(l + ci);
+                    const uint32_t stage = sStage + (uint32_t)(g & 1) * kStage;
+                    bool bad = false;
+                    if (leader) {
+                        tc_fence_after_sync();
+                        bad = !weights_ready(g);
+                        if (!bad) {
+                            for (int c = 0; c < a.nch; ++c)
+                                for (int kk = 0; kk < kHidden / 16; ++kk) {
+                                    const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+                                    umma_bf16(tmem + (uint32_t)(kChunk * c),
+                                              umma_desc_sw128(sH + c * kChan + kb * kBlock + ko),
+                                              umma_desc_sw128(stage + kb * (uint32_t)nn * 128u + ko),
+                                              umma_idesc_bf16(128, nn), kk > 0);
+                                }
+                        }
+                        umma_commit(mma_bar);
+                    }
+                    if (!wait_mma(bad)) { failed = true; break; }
+                    if (leader) release(g);
+                    const int subs = nn / 16;
+                    for (int i = grp; i < a.nch * subs; i += 4) {
+                        const int c = i / subs, s = i - c * subs;
+                        float z[16];
+                        tmem_ld16(lane_addr + (uint32_t)(kChunk * c + 16 * s), z);
+                        if (p < a.P) {
+                            const int col = n0 + 16 * s;
+                            if (c == 0) {
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) z[j] += __ldg(bias + col + j);
+                            }
+                            float *dst = a.nch == 1 ? a.out + p * a.N + col : a.out + (p * 5 + c) * a.N + col;
+                            store8_cs(dst, z);
+                            store8_cs(dst + 8, z + 8);
+                        }
+                    }
+                    tc_fence_before_sync();
+                    __syncthreads();
+                }
             }
         }
-        tc_fence_before_sync();
-        __syncthreads();
     }
 
     if (failed) {
-        if (threadIdx.x == 0) atomicOr(a.status, 1u);
-        // let the MMAs in flight finish (bounded) before the memory goes away
-        mbar_wait_bounded(bar, phase);
+        if (leader) {
+            atomicOr(a.status, 1u);
+            // let the weight copies in flight land (bounded) before the memory goes away
+            for (uint64_t g = consumed; g < issued; ++g) weights_ready(g);
+        }
+        mbar_wait_bounded(mma_bar, mma_phase ^ 1u);   // the phase that was being waited for
         tc_fence_before_sync();
         __syncthreads();
     }
     if (warp == 0) {
         tc_fence_after_sync();
         tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// Writes the weight image: load 0 = W0 ([128][K0], one K-block, columns
+// K0..63 zero), loads 1 .. nl-2 = hidden matrices (two K-blocks), then the
+// output matrix in chunks of kChunk rows (two K-blocks of nn rows each).
+// One thread per 16-byte chunk of a block.
+struct ImageArgs {
+    const __nv_bfloat16 *W[spo_detail::kSurrMaxMats];
+    uint32_t load_off[kSurrMaxLoads];
+    int load_layer[kSurrMaxLoads], load_row0[kSurrMaxLoads], load_rows[kSurrMaxLoads], load_kblocks[kSurrMaxLoads];
+    int in_width[kSurrMaxLoads];
+    int nloads;
+};
+
+__global__ void weight_image_kernel(const __grid_constant__ ImageArgs ia, uint8_t *img) {
+    for (int i = 0; i < ia.nloads; ++i) {
+        const int rows = ia.load_rows[i], kbs = ia.load_kblocks[i], in = ia.in_width[i];
+        const __nv_bfloat16 *W = ia.W[ia.load_layer[i]];
+        const int n = rows * kbs * 8;   // 16-byte chunks
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            const int kb = e / (rows * 8), rem = e - kb * rows * 8;
+            const int r = rem / 8, kc = rem - r * 8;
+            const int k = kb * 64 + kc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (k < in) v = *reinterpret_cast<const uint4 *>(W + (size_t)(ia.load_row0[i] + r) * in + k);
+            *reinterpret_cast<uint4 *>(img + ia.load_off[i] + (uint32_t)kb * (uint32_t)rows * 128u +
+                                       sw128_offset(r, kc * 8)) = v;
+        }
     }
 }
 
@@ -296,33 +432,88 @@ bool surrogate_tc_supported(const SurrMlpView &v, const SurrLevels &lv) {
     return N % 16 == 0 && N >= 16 && N <= 384;
 }
 
-cudaError_t surrogate_fused_tc(const SurrMlpView &v, const __half *grid, const SurrLevels &lv,
-                               const float *pos, int64_t P, float *out, bool values_only,
-                               int num_sms, cudaStream_t stream) {
+SurrImagePlan surrogate_image_plan(const SurrMlpView &v) {
+    SurrImagePlan plan{};
+    uint32_t off = 0;
+    int n = 0;
+    for (int l = 0; l < v.nl - 1; ++l) {
+        plan.off[n] = off;
+        plan.bytes[n] = (l == 0 ? 1u : 2u) * kBlock;
+        off += plan.bytes[n++];
+    }
+    const int N = v.widths[v.nl];
+    for (int n0 = 0; n0 < N; n0 += kChunk) {
+        const int nn = std::min(kChunk, N - n0);
+        plan.off[n] = off;
+        plan.bytes[n] = 2u * (uint32_t)nn * 128u;
+        off += plan.bytes[n++];
+    }
+    plan.nloads = n;
+    plan.total = off;
+    return plan;
+}
+
+cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &plan, uint8_t *img,
+                                  cudaStream_t stream) {
+    ImageArgs ia{};
+    for (int l = 0; l < v.nl; ++l) ia.W[l] = v.W[l];
+    int n = 0;
+    for (int l = 0; l < v.nl - 1; ++l, ++n) {
+        ia.load_off[n] = plan.off[n];
+        ia.load_layer[n] = l;
+        ia.load_row0[n] = 0;
+        ia.load_rows[n] = kHidden;
+        ia.load_kblocks[n] = l == 0 ? 1 : 2;
+        ia.in_width[n] = v.widths[l];
+    }
+    const int N = v.widths[v.nl];
+    for (int n0 = 0; n0 < N; n0 += kChunk, ++n) {
+        ia.load_off[n] = plan.off[n];
+        ia.load_layer[n] = v.nl - 1;
+        ia.load_row0[n] = n0;
+        ia.load_rows[n] = std::min(kChunk, N - n0);
+        ia.load_kblocks[n] = 2;
+        ia.in_width[n] = kHidden;
+    }
+    ia.nloads = n;
+    weight_image_kernel<<<64, 256, 0, stream>>>(ia, img);
+    return cudaGetLastError();
+}
+
+cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const SurrImagePlan &plan,
+                               const __half *grid, const SurrLevels &lv, const float *pos, int64_t P,
+                               float *out, bool values_only, int num_sms, cudaStream_t stream) {
     if (P <= 0) return cudaSuccess;
     FusedArgs a{};
     a.grid = reinterpret_cast<const __half2 *>(grid);
     a.lv = lv;
     a.pos = pos;
     a.P = P;
-    for (int l = 0; l < v.nl; ++l) {
-        a.W[l] = v.W[l];
-        a.b[l] = v.b[l];
+    a.wimg = img;
+    for (int i = 0; i < plan.nloads; ++i) {
+        a.load_off[i] = plan.off[i];
+        a.load_bytes[i] = plan.bytes[i];
     }
+    a.nloads = plan.nloads;
+    for (int l = 0; l < v.nl; ++l) a.b[l] = v.b[l];
     a.nl = v.nl;
     a.K0 = v.widths[0];
     a.N = v.widths[v.nl];
-    a.values_only = values_only ? 1 : 0;
+    a.nch = values_only ? 1 : 5;
     a.out = out;
     cudaError_t e = device_status_address(&a.status);
     if (e != cudaSuccess) return e;
-    const Layout Lo = layout_of(a.nl, a.N);
-    const size_t smem = Lo.bytes + 1024;   // slack for the 1024-byte alignment of the base
-    e = cudaFuncSetAttribute(surrogate_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(surrogate_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    const int64_t ntiles = (P + kTilePos - 1) / kTilePos;
-    const int grid_x = (int)std::min<int64_t>(ntiles, num_sms > 0 ? num_sms : 148);
-    surrogate_fused_kernel<<<grid_x, kThreads, smem, stream>>>(a);
+    // tiles of at most 128 positions, as many per CTA as the waves need, so
+    // that every CTA gets the same number of tiles of nearly equal size
+    const int sms = num_sms > 0 ? num_sms : 148;
+    const int64_t waves = (P + (int64_t)kTile * sms - 1) / ((int64_t)kTile * sms);
+    const int64_t tiles_wanted = waves * sms;
+    a.tile_pos = (int)std::max<int64_t>(1, (P + tiles_wanted - 1) / tiles_wanted);
+    const int64_t ntiles = (P + a.tile_pos - 1) / a.tile_pos;
+    const int grid_x = (int)std::min<int64_t>(ntiles, sms);
+    surrogate_fused_kernel<<<grid_x, kThreads, kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
 
