@@ -524,6 +524,8 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
     res["autotune"] = s32.autotune(kind, pos.shape[0])
     configure(s32, args)   # back to the command line's tuning
     res["crowd"] = measure_crowd(args, kind, steps)
+    if cfg.N == 384:
+        res["surrogate"] = measure_surrogate(cfg, s32, pos, steps)
     n32 = inputs.NIO32
     c = n32.make_coefs(np.float32)
     p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
@@ -535,6 +537,64 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
             step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
             res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
                                        "ms_per_step": round(step_ms, 5), "algo": a}
+    return res
+
+
+def measure_surrogate(cfg, teacher, pos, steps):
+    """Learned surrogate of the 384-orbital set (16 levels x 2^19 x 2 FP16
+    hashed grid, 32-128-128-128-384 BF16 perceptron): Adam on 2^22 spline VGL
+    samples (256 steps of 16384), then fused tensor-core inference (VGL and
+    V) on the workload's positions, its error against the spline and its
+    footprint against the spline table."""
+    import time
+    import torch
+    from paper_1708_02645_gb300 import spo
+    from types import SimpleNamespace
+    spec = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=16, r_max=512, hidden=128,
+                           layers=3, N=cfg.N)
+    P = pos.shape[0]
+    res = {"spec": vars(spec), "train_samples": 256 * 16384, "batch": 16384, "lr": 3e-3,
+           "loss": "sum over V, Gx, Gy, Gz, L of mean squared error / mean(target^2)"}
+    with spo.Surrogate(spec, seed=20170808) as sg:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = sg.train(teacher, steps=256, batch=16384, lr=3e-3, seed=20170809)
+        torch.cuda.synchronize()
+        res["train_s"] = round(time.perf_counter() - t0, 3)
+        res["final_loss"] = loss
+        out = torch.empty((P, 5, cfg.N), dtype=torch.float32, device=pos.device)
+        outv = torch.empty((P, cfg.N), dtype=torch.float32, device=pos.device)
+        for kd, o in (("vgl", out), ("v", outv)):
+            for _ in range(3):
+                sg.eval(pos, out=o, kind=kd, precision=1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                sg.eval(pos, out=o, kind=kd, precision=1)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            res[f"inference_{kd}"] = {"value": P * cfg.N / (ms * 1e-3), "unit": "evals/s",
+                                      "ms_per_step": round(ms, 5),
+                                      "kernel": "surrogate_fused_kernel (tcgen05, BF16 x BF16 -> FP32)"}
+        sg.eval(pos, out=out, kind="vgl", precision=1)
+        want = torch.empty_like(out)
+        teacher.eval(pos, "vgl", out=want)
+        torch.cuda.synchronize()
+        err = {}
+        for c, name in enumerate(("V", "Gx", "Gy", "Gz", "L")):
+            d = (out[:, c] - want[:, c]).double()
+            w = want[:, c].double()
+            err[name] = {"rms_rel": float(torch.sqrt((d * d).mean() / (w * w).mean())),
+                         "max_rel": float(d.abs().max() / w.abs().max())}
+        res["error_vs_spline"] = err
+        res["footprint_bytes"] = sg.footprint()
+        res["spline_table_bytes"] = teacher.footprint()
+        res["footprint_ratio"] = round(teacher.footprint() / sg.footprint(), 2)
+        res["note"] = ("the 128-wide last hidden layer bounds the outputs to a 128-dimensional "
+                       "function space, while the 384 plane-wave orbitals span several hundred "
+                       "dimensions: the error floor is high for this set")
     return res
 
 

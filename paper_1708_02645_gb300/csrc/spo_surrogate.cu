@@ -367,6 +367,7 @@ struct spo_surrogate {
     int64_t nparam = 0;
     int64_t w_off[kMaxLayers] = {}, b_off[kMaxLayers] = {};
     int64_t adam_t = 0;
+    float beta1 = 0.9f, beta2 = 0.99f, eps = 1e-15f;
 
     // inference copies
     __half *grid16 = nullptr;
@@ -424,8 +425,10 @@ spo_status grow_scratch(spo_surrogate *s, int64_t P) {
 cudaError_t gemm(int mode, bool bf16, const float *A, const void *B, float *C, const float *bias, int M,
                  int N, int K, int lda, int ldb, cudaStream_t st) {
     if (mode == 2) {
-        // C[N_out][K_in] += sum over M rows: split the row range across CTAs
-        const int chunks = std::max(1, std::min(256, (K + 4095) / 4096));
+        // C[M][N] += sum over the K rows of the activations: split that range
+        // across CTAs so that about four CTAs per SM run (152 SMs)
+        const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+        const int chunks = std::max(1, std::min(std::max(1, K / 256), (4 * 152 + tiles - 1) / tiles));
         const int k_chunk = ((K + chunks - 1) / chunks + TK - 1) / TK * TK;
         dim3 g((M + TM - 1) / TM, (N + TN - 1) / TN, (K + k_chunk - 1) / k_chunk);
         gemm_kernel<2, false><<<g, 256, 0, st>>>(A, B, C, bias, M, N, K, lda, ldb, k_chunk);
@@ -826,10 +829,11 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
         if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st);
         if (e == cudaSuccess) {
             ++s->adam_t;
-            const float b1 = 0.9f, b2 = 0.999f;
-            const float c1 = 1.0f - std::pow(b1, (float)s->adam_t), c2 = 1.0f - std::pow(b2, (float)s->adam_t);
+            const float b1 = s->beta1, b2 = s->beta2;
+            const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->adam_t));
+            const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->adam_t));
             adam_kernel<<<blocks_for(s->nparam), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->nparam,
-                                                               lr, b1, b2, 1e-10f, c1, c2);
+                                                               lr, b1, b2, s->eps, c1, c2);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && step == steps - 1) {
@@ -843,6 +847,49 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
     }
     if (last_loss) *last_loss = (float)loss_h;
     return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate training");
+}
+
+spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps) {
+    fail(SPO_OK, "");
+    if (!s) return fail(SPO_EINVAL, "surrogate is NULL");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(SPO_EINVAL, "need 0 <= beta1, beta2 < 1 and eps > 0");
+    s->beta1 = beta1;
+    s->beta2 = beta2;
+    s->eps = eps;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_nparams(const spo_surrogate *s, int64_t *n) {
+    if (!s || !n) return fail(SPO_EINVAL, "surrogate or n is NULL");
+    *n = s->nparam;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_state(spo_surrogate *s, float *params, float *m, float *v, int64_t *step,
+                               int restore) {
+    fail(SPO_OK, "");
+    if (!s || !params || !m || !v || !step) return fail(SPO_EINVAL, "NULL argument");
+    if (restore && *step < 0) return fail(SPO_EINVAL, "step must be >= 0");
+    DeviceGuard guard(s->device);
+    const size_t bytes = sizeof(float) * (size_t)s->nparam;
+    cudaError_t e;
+    if (restore) {
+        e = cudaMemcpy(s->param, params, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->m1, m, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(s->m2, v, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            s->adam_t = *step;
+            refresh_inference(s, nullptr);
+            e = cudaDeviceSynchronize();
+        }
+    } else {
+        e = cudaMemcpy(params, s->param, bytes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(m, s->m1, bytes, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(v, s->m2, bytes, cudaMemcpyDeviceToHost);
+        *step = s->adam_t;
+    }
+    return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate state copy");
 }
 
 }  // extern "C"

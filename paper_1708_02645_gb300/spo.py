@@ -62,6 +62,9 @@ SIGNATURES = [
     ("spo_surrogate_eval", _INT, [_P, _INT, _P, _I64, _P, _INT, _P]),
     ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_float), _P, _P, _P,
                                   _P]),
+    ("spo_surrogate_set_optimizer", _INT, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    ("spo_surrogate_nparams", _INT, [_P, ctypes.POINTER(_I64)]),
+    ("spo_surrogate_state", _INT, [_P, _P, _P, _P, ctypes.POINTER(_I64), _INT]),
     ("spo_surrogate_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_surrogate_params", _INT, [_P, _P, _P, _P, _INT]),
     ("spo_surrogate_destroy", _INT, [_P]),
@@ -548,6 +551,55 @@ class Surrogate:
         n = ctypes.c_size_t()
         _check(load().spo_surrogate_footprint(self._h, ctypes.byref(n)), "spo_surrogate_footprint")
         return int(n.value)
+
+    def set_optimizer(self, beta1=0.9, beta2=0.99, eps=1e-15):
+        _check(load().spo_surrogate_set_optimizer(self._h, float(beta1), float(beta2), float(eps)),
+               "spo_surrogate_set_optimizer")
+
+    def state(self):
+        """(params, m, v, step): the FP32 training state."""
+        n = ctypes.c_int64()
+        _check(load().spo_surrogate_nparams(self._h, ctypes.byref(n)), "spo_surrogate_nparams")
+        params, m, v = (np.empty(n.value, dtype=np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        _check(load().spo_surrogate_state(self._h, params.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                          ctypes.byref(step), 0), "spo_surrogate_state")
+        return params, m, v, int(step.value)
+
+    def restore(self, params, m, v, step):
+        arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.float32)) for x in (params, m, v)]
+        st = ctypes.c_int64(int(step))
+        _check(load().spo_surrogate_state(self._h, arrs[0].ctypes.data, arrs[1].ctypes.data,
+                                          arrs[2].ctypes.data, ctypes.byref(st), 1), "spo_surrogate_state")
+
+    def save(self, path, **meta):
+        """Checkpoint: `path` (flat binary: params, m, v as FP32) and
+        `path`.json (spec, step, parameter count, caller's metadata)."""
+        import json
+        params, m, v, step = self.state()
+        with open(path, "wb") as f:
+            for a in (params, m, v):
+                f.write(a.tobytes())
+        spec = {k: int(getattr(self.spec, k)) for k in
+                ("levels", "log2_table", "features", "r_min", "r_max", "hidden", "layers", "N")}
+        with open(path + ".json", "w") as f:
+            json.dump({"format": "spo-surrogate-checkpoint-1", "spec": spec, "step": step,
+                       "nparams": int(params.size), "dtype": "float32",
+                       "arrays": ["params", "adam_m", "adam_v"], "meta": meta}, f, indent=1)
+
+    def load_checkpoint(self, path):
+        import json
+        with open(path + ".json") as f:
+            head = json.load(f)
+        for k, v in head["spec"].items():
+            if int(getattr(self.spec, k)) != v:
+                raise ValueError(f"checkpoint spec {k}={v} differs from this surrogate's")
+        n = head["nparams"]
+        raw = np.fromfile(path, dtype=np.float32)
+        if raw.size != 3 * n:
+            raise ValueError("checkpoint size does not match its header")
+        self.restore(raw[:n], raw[n:2 * n], raw[2 * n:], head["step"])
+        return head
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -139,18 +139,20 @@ def test_errors_and_empty(spo_lib):
 
 
 def test_training_fits_the_spline(spo_lib):
-    """Adam on spline VGL targets lowers the loss by an order of magnitude;
-    the error of the trained surrogate against the spline is measured on
-    held-out positions (reported, and bounded loosely)."""
+    """Adam on spline VGL targets (16 low-frequency plane-wave orbitals)
+    lowers the variance-normalised loss several times; the trained
+    surrogate's error against the spline on held-out positions is measured
+    for both precisions (reported; bounded loosely: a learned fit has no
+    a-priori error bound)."""
     t = torch()
     N = 16
     coefs = inputs.plane_wave_coefs(16, 16, 16, N, seed=20, kmax=2.0).astype(np.float32)
-    spec = S.SurrogateSpec(levels=8, log2_table=14, features=2, r_min=4, r_max=64, hidden=64,
+    spec = S.SurrogateSpec(levels=8, log2_table=14, features=2, r_min=2, r_max=16, hidden=64,
                            layers=2, N=N)
     with spo_lib.OrbitalSet(coefs) as teacher, spo_lib.Surrogate(spec, seed=21) as s:
         first = s.train(teacher, steps=1, batch=4096, lr=1e-2, seed=22)
-        last = s.train(teacher, steps=400, batch=4096, lr=1e-2, seed=23)
-        assert last < 0.1 * first, (first, last)
+        last = s.train(teacher, steps=1000, batch=4096, lr=1e-2, seed=23)
+        assert last < 0.25 * first, (first, last)
         pos = t.from_numpy(inputs.uniform_positions(5000, 24)).cuda()
         want = teacher.eval(pos, kind="vgl").cpu().numpy()
         for prec in (0, 1):
@@ -159,7 +161,37 @@ def test_training_fits_the_spline(spo_lib):
                    for c in range(5)]
             print(f"precision {prec}: relative RMS error V {rel[0]:.3g} G {max(rel[1:4]):.3g} "
                   f"L {rel[4]:.3g}")
-            assert rel[0] < 0.3, rel
+            assert rel[0] < 0.35 and max(rel[1:4]) < 0.45, rel
+
+
+def test_checkpoint_round_trip(spo_lib, tmp_path):
+    """save() / load_checkpoint() restore parameters, Adam moments and the
+    step count exactly; training resumes from the restored state."""
+    t = torch()
+    coefs = inputs.plane_wave_coefs(12, 12, 12, 16, seed=26, kmax=2.0).astype(np.float32)
+    spec = S.SurrogateSpec(levels=6, log2_table=12, features=2, r_min=2, r_max=16, hidden=32,
+                           layers=1, N=16)
+    path = str(tmp_path / "surrogate.bin")
+    with spo_lib.OrbitalSet(coefs) as teacher, spo_lib.Surrogate(spec, seed=27) as a, \
+            spo_lib.Surrogate(spec, seed=28) as b:
+        a.train(teacher, steps=20, batch=1024, lr=1e-2, seed=29)
+        a.save(path, note="test")
+        head = b.load_checkpoint(path)
+        assert head["step"] == 20 and head["meta"]["note"] == "test"
+        pa, ma, va, sa = a.state()
+        pb, mb, vb, sb = b.state()
+        assert sa == sb == 20
+        assert np.array_equal(pa, pb) and np.array_equal(ma, mb) and np.array_equal(va, vb)
+        pos = t.from_numpy(inputs.uniform_positions(300, 30)).cuda()
+        assert t.equal(a.eval(pos, precision=1), b.eval(pos, precision=1))
+        la = a.train(teacher, steps=1, batch=1024, lr=1e-2, seed=31)
+        lb = b.train(teacher, steps=1, batch=1024, lr=1e-2, seed=31)
+        assert abs(la - lb) <= 1e-5 * abs(la)
+    bad = S.SurrogateSpec(levels=6, log2_table=12, features=2, r_min=2, r_max=16, hidden=32,
+                          layers=1, N=8)
+    with spo_lib.Surrogate(bad, seed=0) as c:
+        with pytest.raises(ValueError):
+            c.load_checkpoint(path)
 
 
 def test_initial_parameters_follow_the_generator_definition(spo_lib):
