@@ -175,10 +175,140 @@ __device__ __forceinline__ void make_xaxis(float r, const GridAxis &g, XAxis &ax
 // first term of every sum is a product and each later term one FMA, in a
 // fixed order, so all kernels produce the same bits for the same position
 // and orbitals.
+// Packed form for an even number of orbitals: every operation acts on two
+// orbitals at once (fma.rn.f32x2 / mul.rn.f32x2 on sm_100 and later), each
+// lane rounding exactly as the scalar form, so the results are the same bits.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
+template <int KIND, int V, int A, typename Load>
+__device__ __forceinline__ void window_x_node_packed(float xw, float xd, float xdd, const Axis &Y,
+                                                     const Axis &Z, Load &load,
+                                                     float (&acc)[Rows<KIND>::value][V]) {
+    constexpr int NY = KIND == SPO_KIND_V ? 1 : (KIND == SPO_KIND_VGL ? 5 : 6);
+    constexpr int NP = V / 2;
+    float2 ys[NY][NP];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        float cv[4][V];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) load(A, b, g, cv[g]);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float2 c0 = make_float2(cv[0][2 * k], cv[0][2 * k + 1]);
+            const float2 c1 = make_float2(cv[1][2 * k], cv[1][2 * k + 1]);
+            const float2 c2 = make_float2(cv[2][2 * k], cv[2][2 * k + 1]);
+            const float2 c3 = make_float2(cv[3][2 * k], cv[3][2 * k + 1]);
+            float2 zv = __fmul2_rn(bc2(Z.w[0]), c0);
+            zv = __ffma2_rn(bc2(Z.w[1]), c1, zv);
+            zv = __ffma2_rn(bc2(Z.w[2]), c2, zv);
+            zv = __ffma2_rn(bc2(Z.w[3]), c3, zv);
+            float2 zd = make_float2(0.0f, 0.0f), zdd = make_float2(0.0f, 0.0f);
+            if constexpr (KIND != SPO_KIND_V) {
+                zd = __fmul2_rn(bc2(Z.d[0]), c0);
+                zd = __ffma2_rn(bc2(Z.d[1]), c1, zd);
+                zd = __ffma2_rn(bc2(Z.d[2]), c2, zd);
+                zd = __ffma2_rn(bc2(Z.d[3]), c3, zd);
+                zdd = __fmul2_rn(bc2(Z.dd[0]), c0);
+                zdd = __ffma2_rn(bc2(Z.dd[1]), c1, zdd);
+                zdd = __ffma2_rn(bc2(Z.dd[2]), c2, zdd);
+                zdd = __ffma2_rn(bc2(Z.dd[3]), c3, zdd);
+            }
+            if (b == 0) {
+                ys[0][k] = __fmul2_rn(bc2(Y.w[0]), zv);
+                if constexpr (KIND != SPO_KIND_V) {
+                    ys[1][k] = __fmul2_rn(bc2(Y.d[0]), zv);
+                    ys[2][k] = __fmul2_rn(bc2(Y.dd[0]), zv);
+                    ys[3][k] = __fmul2_rn(bc2(Y.w[0]), zd);
+                    if constexpr (KIND == SPO_KIND_VGH) {
+                        ys[4][k] = __fmul2_rn(bc2(Y.d[0]), zd);
+                        ys[5][k] = __fmul2_rn(bc2(Y.w[0]), zdd);
+                    } else {
+                        ys[4][k] = __fmul2_rn(bc2(Y.w[0]), zdd);
+                    }
+                }
+            } else {
+                ys[0][k] = __ffma2_rn(bc2(Y.w[b]), zv, ys[0][k]);
+                if constexpr (KIND != SPO_KIND_V) {
+                    ys[1][k] = __ffma2_rn(bc2(Y.d[b]), zv, ys[1][k]);
+                    ys[2][k] = __ffma2_rn(bc2(Y.dd[b]), zv, ys[2][k]);
+                    ys[3][k] = __ffma2_rn(bc2(Y.w[b]), zd, ys[3][k]);
+                    if constexpr (KIND == SPO_KIND_VGH) {
+                        ys[4][k] = __ffma2_rn(bc2(Y.d[b]), zd, ys[4][k]);
+                        ys[5][k] = __ffma2_rn(bc2(Y.w[b]), zdd, ys[5][k]);
+                    } else {
+                        ys[4][k] = __ffma2_rn(bc2(Y.w[b]), zdd, ys[4][k]);
+                    }
+                }
+            }
+        }
+    }
+    // x stage
+    const float2 w2 = bc2(xw), d2 = bc2(xd), dd2 = bc2(xdd);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        constexpr int NC = Rows<KIND>::value;
+        float2 a[NC];
+        if constexpr (A == 0) {
+            a[0] = __fmul2_rn(w2, ys[0][k]);                        // v
+            if constexpr (KIND == SPO_KIND_VGH) {
+                a[1] = __fmul2_rn(d2, ys[0][k]);                    // gx
+                a[2] = __fmul2_rn(w2, ys[1][k]);                    // gy
+                a[3] = __fmul2_rn(w2, ys[3][k]);                    // gz
+                a[4] = __fmul2_rn(dd2, ys[0][k]);                   // hxx
+                a[5] = __fmul2_rn(d2, ys[1][k]);                    // hxy
+                a[6] = __fmul2_rn(d2, ys[3][k]);                    // hxz
+                a[7] = __fmul2_rn(w2, ys[2][k]);                    // hyy
+                a[8] = __fmul2_rn(w2, ys[4][k]);                    // hyz
+                a[9] = __fmul2_rn(w2, ys[5][k]);                    // hzz
+            } else if constexpr (KIND == SPO_KIND_VGL) {
+                a[1] = __fmul2_rn(d2, ys[0][k]);
+                a[2] = __fmul2_rn(w2, ys[1][k]);
+                a[3] = __fmul2_rn(w2, ys[3][k]);
+                float2 l = __fmul2_rn(dd2, ys[0][k]);
+                l = __ffma2_rn(w2, ys[2][k], l);
+                a[4] = __ffma2_rn(w2, ys[4][k], l);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) a[c] = make_float2(acc[c][2 * k], acc[c][2 * k + 1]);
+            a[0] = __ffma2_rn(w2, ys[0][k], a[0]);
+            if constexpr (KIND == SPO_KIND_VGH) {
+                a[1] = __ffma2_rn(d2, ys[0][k], a[1]);
+                a[2] = __ffma2_rn(w2, ys[1][k], a[2]);
+                a[3] = __ffma2_rn(w2, ys[3][k], a[3]);
+                a[4] = __ffma2_rn(dd2, ys[0][k], a[4]);
+                a[5] = __ffma2_rn(d2, ys[1][k], a[5]);
+                a[6] = __ffma2_rn(d2, ys[3][k], a[6]);
+                a[7] = __ffma2_rn(w2, ys[2][k], a[7]);
+                a[8] = __ffma2_rn(w2, ys[4][k], a[8]);
+                a[9] = __ffma2_rn(w2, ys[5][k], a[9]);
+            } else if constexpr (KIND == SPO_KIND_VGL) {
+                a[1] = __ffma2_rn(d2, ys[0][k], a[1]);
+                a[2] = __ffma2_rn(w2, ys[1][k], a[2]);
+                a[3] = __ffma2_rn(w2, ys[3][k], a[3]);
+                float2 l = __ffma2_rn(dd2, ys[0][k], a[4]);
+                l = __ffma2_rn(w2, ys[2][k], l);
+                a[4] = __ffma2_rn(w2, ys[4][k], l);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            acc[c][2 * k] = a[c].x;
+            acc[c][2 * k + 1] = a[c].y;
+        }
+    }
+}
+
 template <int KIND, int V, int A, typename Load>
 __device__ __forceinline__ void window_x_node(float xw, float xd, float xdd, const Axis &Y,
                                               const Axis &Z, Load &load,
                                               float (&acc)[Rows<KIND>::value][V]) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    if constexpr (V % 2 == 0) {
+        window_x_node_packed<KIND, V, A>(xw, xd, xdd, Y, Z, load, acc);
+        return;
+    }
+#endif
     constexpr int NY = KIND == SPO_KIND_V ? 1 : (KIND == SPO_KIND_VGL ? 5 : 6);
     // y-stage partial sums for this x node
     //   VGH: wy*v, dy*v, ddy*v, wy*dz, dy*dz, wy*ddz
