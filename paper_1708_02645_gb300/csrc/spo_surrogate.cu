@@ -249,20 +249,26 @@ struct ChannelWeights {
     float w[5];
 };
 
-// g = 2 w_c (out - target) / (P N); loss accumulated in FP64
+// g = 2 w_c (out - target) / (P N) in FP32; the loss sum_c w_c mean(d^2)
+// is summed per thread in FP32, per block and across blocks in FP64.  Rows
+// (position, channel) go one per block iteration, orbitals across threads.
 __global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ target, int64_t P,
                             int64_t N, ChannelWeights cw, float *__restrict__ g, double *loss) {
     __shared__ double red[256];
-    double local = 0.0;
     const double inv = 1.0 / ((double)P * (double)N);
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P * 5 * N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)((e / N) % 5);
-        const float d = out[e] - target[e];
-        g[e] = (float)(2.0 * cw.w[ch] * d * inv);
-        local += (double)cw.w[ch] * d * d * inv;
+    float local = 0.0f;
+    for (int64_t row = blockIdx.x; row < P * 5; row += gridDim.x) {
+        const int ch = (int)(row % 5);
+        const float w = cw.w[ch], gs = (float)(2.0 * cw.w[ch] * inv);
+        const float *o = out + row * N, *t = target + row * N;
+        float *gr = g + row * N;
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+            const float d = o[j] - t[j];
+            gr[j] = gs * d;
+            local = fmaf(w * d, d, local);
+        }
     }
-    red[threadIdx.x] = local;
+    red[threadIdx.x] = (double)local * inv;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
@@ -271,15 +277,30 @@ __global__ void loss_kernel(const float *__restrict__ out, const float *__restri
     if (threadIdx.x == 0) atomicAdd(loss, red[0]);
 }
 
-// mean of target_c^2 over positions and orbitals, per channel (sums in FP64)
+// sums of target_c^2 over positions and orbitals, per channel (pw[0..4])
 __global__ void channel_power_kernel(const float *__restrict__ target, int64_t P, int64_t N,
                                      double *pw) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P * 5 * N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int ch = (int)((e / N) % 5);
-        const double v = target[e];
-        atomicAdd(pw + ch, v * v);
+    __shared__ double red[5][256];
+    double local[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t row = blockIdx.x; row < P * 5; row += gridDim.x) {
+        const int ch = (int)(row % 5);
+        const float *t = target + row * N;
+        float acc = 0.0f;
+        for (int64_t j = threadIdx.x; j < N; j += blockDim.x) acc = fmaf(t[j], t[j], acc);
+#pragma unroll
+        for (int c = 0; c < 5; ++c)
+            if (c == ch) local[c] += acc;
     }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) red[c][threadIdx.x] = local[c];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 5) atomicAdd(pw + threadIdx.x, red[threadIdx.x][0]);
 }
 
 // gb[j] += sum_p gz[p][0][j]; blockIdx.y takes a slice of the positions
@@ -498,7 +519,7 @@ cudaError_t channel_weights_for(spo_surrogate *s, const float *target, int64_t P
     const int64_t N = s->spec.N;
     cudaError_t e = cudaMemsetAsync(s->dacc, 0, sizeof(double) * 8, st);
     if (e != cudaSuccess) return e;
-    channel_power_kernel<<<blocks_for(P * 5 * N), 256, 0, st>>>(target, P, N, s->dacc);
+    channel_power_kernel<<<(unsigned)std::min<int64_t>(P * 5, 152 * 8), 256, 0, st>>>(target, P, N, s->dacc);
     double pw[8];
     e = cudaMemcpyAsync(pw, s->dacc, sizeof(double) * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -519,7 +540,8 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     cudaError_t e = forward_fp32(s, pos, P, out, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dacc, 0, sizeof(double), st);
     if (e == cudaSuccess) {
-        loss_kernel<<<blocks_for(P * 5 * N), 256, 0, st>>>(out, target, P, N, cw, s->gbuf[1], s->dacc);
+        loss_kernel<<<(unsigned)std::min<int64_t>(P * 5, 152 * 8), 256, 0, st>>>(out, target, P, N, cw, s->gbuf[1],
+                                                                                  s->dacc);
         e = cudaGetLastError();
     }
     // g = gbuf[gi] is d loss / d output of layer l; the two buffers alternate
