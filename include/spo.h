@@ -257,6 +257,14 @@ spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const float *pos,
  *   Between replays the caller may change the contents of the pos buffers
  *   (new moves), not the items themselves.
  * Calls on one plan must be ordered (one stream): they share its scratch.
+ *
+ * spo_eval_batch(sets, nsets, items, nitems, kind, stream): one-call form.
+ *   When the sets can share a plan (at most SPO_BATCH_MAX_SETS sets of one
+ *   storage type on one device, each with >= 32 padded orbitals) it builds
+ *   a temporary plan, queues the batched evaluation and waits for the
+ *   stream before freeing the plan (synchronous); otherwise it queues one
+ *   spo_eval_ex per walker (asynchronous).  Keep a plan (spo_batch_*) to
+ *   avoid the allocation and the wait.
  */
 #define SPO_BATCH_MAX_SETS 8
 
@@ -278,6 +286,24 @@ spo_status spo_batch_graph(spo_batch *plan, spo_kind kind, const spo_work *items
                            void *stream);
 spo_status spo_batch_launch(spo_batch *plan, void *stream);
 spo_status spo_batch_destroy(spo_batch *plan);
+spo_status spo_eval_batch(const spo_set *const *sets, int nsets, const spo_work *items, int nitems,
+                          spo_kind kind, void *stream);
+
+/*
+ * Interpolating coefficients.  The table spo_create takes holds B-spline
+ * coefficients; grid samples f(m / n) used as coefficients give a smoothed
+ * f that does not pass through the samples.  spo_prefilter turns samples
+ * into the coefficients of the interpolating spline, in place: along each
+ * axis (c[m-1] + 4 c[m] + c[m+1]) / 6 = f[m], periodic (B3 at offsets -1, 0,
+ * 1; the prefilter of the uniform cubic B-spline, done as a causal and an
+ * anticausal recursion with pole sqrt(3) - 2 per axis, in FP64).
+ *
+ * spo_prefilter(grid, N, data, dtype, stream): data is a device array
+ *   [nx][ny][nz][N] of dtype SPO_F64 or SPO_F32 (C order, orbital fastest),
+ *   owned by the caller; queued on stream.  Feed the result to spo_create
+ *   with coefs_on_device = 1.
+ */
+spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype dtype, void *stream);
 
 /*
  * Learned surrogate — a small learned function of the position standing in

@@ -156,3 +156,24 @@ def spo_ratio_condition(coefs: np.ndarray, pos: np.ndarray, rows: np.ndarray,
     rows = np.abs(np.asarray(rows, dtype=np.float64))
     idx = np.arange(b.shape[0]) if row_of is None else np.asarray(row_of)
     return np.einsum("pj,pj->p", rows[idx], b)
+
+
+def prefilter(samples: np.ndarray) -> np.ndarray:
+    """Interpolating B-spline coefficients of periodic grid samples.
+
+    The coefficients the spline of which passes through the samples at the
+    grid nodes: along every axis the spline's value at node m is
+    (c[m-1] + 4 c[m] + c[m+1]) / 6 (B3 at offsets -1, 0, 1), so c is the
+    samples with that circulant operator inverted on each axis.  The inverse
+    is taken exactly in Fourier space: the operator's eigenvalue at
+    frequency k is (4 + 2 cos(2 pi k / n)) / 6 (the reading of the
+    coefficients-vs-samples question that prefilters, with the DFT divided
+    by prod_d (2 + cos th_d) / 3).  samples: [nx, ny, nz, N]; FP64 result."""
+    c = np.asarray(samples, dtype=np.float64)
+    for ax in range(3):
+        n = c.shape[ax]
+        sym = (4.0 + 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)) / 6.0
+        shape = [1] * c.ndim
+        shape[ax] = n
+        c = np.real(np.fft.ifft(np.fft.fft(c, axis=ax) / sym.reshape(shape), axis=ax))
+    return c

@@ -320,6 +320,47 @@ spo_status spo_batch_eval(spo_batch *b, spo_kind kind, const spo_work *items, in
     return st;
 }
 
+spo_status spo_eval_batch(const spo_set *const *sets, int nsets, const spo_work *items, int nitems,
+                          spo_kind kind, void *stream) {
+    fail(SPO_OK, "");
+    if (!sets || nsets < 1 || (nitems > 0 && !items) || nitems < 0)
+        return fail(SPO_EINVAL, "need sets, nsets >= 1 and an item table");
+    if (kind != SPO_KIND_V && kind != SPO_KIND_VGL && kind != SPO_KIND_VGH)
+        return fail(SPO_EINVAL, "invalid kind %d", (int)kind);
+    if (nitems == 0) return SPO_OK;
+    bool planned = nsets <= SPO_BATCH_MAX_SETS;
+    int64_t total = 0;
+    for (int i = 0; i < nsets; ++i) {
+        if (!sets[i]) return fail(SPO_EINVAL, "set %d is NULL", i);
+        planned = planned && sets[i]->has_block_map && sets[i]->storage == sets[0]->storage &&
+                  sets[i]->device == sets[0]->device;
+    }
+    for (int k = 0; k < nitems; ++k) {
+        if (items[k].set < 0 || items[k].set >= nsets) return fail(SPO_EINVAL, "item %d: bad set", k);
+        if (items[k].P < 0) return fail(SPO_EINVAL, "item %d: P < 0", k);
+        total += items[k].P;
+    }
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (!planned) {
+        // sets the one-launch plan cannot take: one evaluation per walker
+        for (int k = 0; k < nitems; ++k) {
+            if (items[k].P == 0) continue;
+            const spo_status st = spo_eval_ex(sets[items[k].set], kind, items[k].pos, items[k].P,
+                                              items[k].out, stream, SPO_ALGO_AUTO);
+            if (st != SPO_OK) return st;
+        }
+        return SPO_OK;
+    }
+    spo_batch *plan = nullptr;
+    spo_status st = spo_batch_create(sets, nsets, std::max<int64_t>(total, 1), nitems, &plan);
+    if (st != SPO_OK) return st;
+    st = spo_batch_eval(plan, kind, items, nitems, stream);
+    if (st == SPO_OK && cudaStreamSynchronize(cs) != cudaSuccess)
+        st = fail(SPO_ECUDA, "stream synchronisation failed");
+    const spo_status ds = spo_batch_destroy(plan);
+    return st != SPO_OK ? st : ds;
+}
+
 spo_status spo_batch_graph(spo_batch *b, spo_kind kind, const spo_work *items, int nitems,
                            void *stream) {
     fail(SPO_OK, "");

@@ -50,12 +50,14 @@ SIGNATURES = [
     ("spo_batch_graph", _INT, [_P, _INT, _P, _INT, _P]),
     ("spo_batch_launch", _INT, [_P, _P]),
     ("spo_batch_destroy", _INT, [_P]),
+    ("spo_eval_batch", _INT, [_P, _INT, _P, _INT, _INT, _P]),
     ("spo_device_status", _INT, [ctypes.POINTER(ctypes.c_uint), _INT, _P]),
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_set_param", _INT, [_P, _INT, _I64]),
     ("spo_get_param", _INT, [_P, _INT, ctypes.POINTER(_I64)]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
+    ("spo_prefilter", _INT, [_P, _I64, _P, _INT, _P]),
     ("spo_surrogate_create", _INT, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
     ("spo_surrogate_train", _INT, [_P, _P, _I64, _I64, ctypes.c_float, _P, ctypes.c_uint64, _P,
                                    ctypes.POINTER(ctypes.c_float)]),
@@ -387,6 +389,37 @@ class OrbitalSet:
 class _Work(ctypes.Structure):
     _fields_ = [("set", ctypes.c_int32), ("reserved", ctypes.c_int32), ("P", ctypes.c_int64),
                 ("pos", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+def prefilter(samples, stream=None):
+    """Interpolating B-spline coefficients from periodic grid samples, in
+    place: samples is a CUDA tensor [nx, ny, nz, N] (float64 or float32)."""
+    torch = _torch()
+    if not samples.is_cuda or not samples.is_contiguous() or samples.dim() != 4:
+        raise TypeError("samples must be a contiguous CUDA tensor [nx, ny, nz, N]")
+    dt = {torch.float64: F64, torch.float32: F32}.get(samples.dtype)
+    if dt is None:
+        raise TypeError("samples must be float64 or float32")
+    g = _Grid(*[int(x) for x in samples.shape[:3]])
+    _check(load().spo_prefilter(ctypes.byref(g), int(samples.shape[3]), ctypes.c_void_p(samples.data_ptr()),
+                                dt, _stream_handle(stream)), "spo_prefilter")
+    return samples
+
+
+def eval_batch(sets, items, kind="vgh", stream=None):
+    """One-call batched evaluation (spo_eval_batch): items are (set index,
+    pos [P, 3] CUDA FP32, out CUDA FP32)."""
+    k = KINDS[kind] if isinstance(kind, str) else int(kind)
+    arr = (ctypes.c_void_p * len(sets))(*[s.handle.value for s in sets])
+    table = (_Work * max(1, len(items)))()
+    for i, (si, pos, out) in enumerate(items):
+        table[i].set = int(si)
+        table[i].reserved = 0
+        table[i].P = int(pos.shape[0])
+        table[i].pos = pos.data_ptr()
+        table[i].out = out.data_ptr()
+    _check(load().spo_eval_batch(arr, len(sets), table, len(items), k, _stream_handle(stream)),
+           "spo_eval_batch")
 
 
 class Batch:

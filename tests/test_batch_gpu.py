@@ -106,3 +106,24 @@ def test_batch_rejects_bad_plans_and_items(spo_lib):
             b.launch()
     for s in sets + [small]:
         s.close()
+
+
+@pytest.mark.parametrize("small_set", [False, True])
+def test_one_call_eval_batch(spo_lib, small_set):
+    """spo_eval_batch equals per-walker evaluations bit for bit, through a
+    temporary plan (sets the plan takes) and through per-walker calls (a set
+    with fewer than 32 padded orbitals, which the plan cannot take)."""
+    t = torch()
+    sets, coefs, walkers = make_crowd(spo_lib, nwalk=17, seed=91)
+    if small_set:
+        c = inputs.plane_wave_coefs(9, 10, 11, 13, seed=95).astype(np.float32)
+        sets.append(spo_lib.OrbitalSet(c))
+        walkers = [(w % 4, p) for w, (_, p) in enumerate(walkers)]
+    outs = outputs_for(sets, walkers, "vgh")
+    spo_lib.eval_batch(sets, [(k, p, o) for (k, p), o in zip(walkers, outs)], "vgh")
+    t.cuda.synchronize()
+    assert spo_lib.device_status() == 0
+    for (k, p), o in zip(walkers, outs):
+        if p.shape[0] == 0:
+            continue
+        assert t.equal(o, sets[k].eval(p, "vgh"))

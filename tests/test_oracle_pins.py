@@ -359,3 +359,41 @@ def test_ratio_reduces_to_values_for_unit_rows(oracle_lib):
     for j in range(4):
         rho = oracle.spo_ratio(c, pos, eye[j:j + 1], row_of=np.zeros(12, dtype=int))
         assert np.array_equal(rho, v[:, j])
+
+
+def test_prefilter_interpolates_at_the_nodes(oracle_lib):
+    """The spline of the prefiltered coefficients passes through the samples
+    at every grid node (V), independently checked by the oracle's window
+    sums; on tiny grids the prefilter also equals the dense solve of the
+    per-axis cyclic systems (c[m-1] + 4 c[m] + c[m+1]) / 6 = f[m]."""
+    import oracle
+    ns, N = (5, 6, 7), 3
+    f = inputs.uniform_coefs(*ns, N, seed=71)
+    c = oracle.prefilter(f)
+    nodes = np.stack(np.meshgrid(*[np.arange(n) / n for n in ns], indexing="ij"), -1).reshape(-1, 3)
+    v = oracle.spo_eval(c, nodes, KIND_V)
+    assert np.abs(v - f.reshape(-1, N)).max() < 1e-12
+    # dense per-axis solve
+    d = np.array(f)
+    for ax, n in enumerate(ns):
+        A = np.zeros((n, n))
+        for j in range(n):
+            A[j, (j - 1) % n] += 1 / 6
+            A[j, j] += 4 / 6
+            A[j, (j + 1) % n] += 1 / 6
+        d = np.moveaxis(np.linalg.solve(A, np.moveaxis(d, ax, 0).reshape(n, -1)).reshape(
+            np.moveaxis(d, ax, 0).shape), 0, ax)
+    assert np.abs(d - c).max() < 1e-12
+
+
+def test_prefilter_plane_wave_symbol(oracle_lib):
+    """Samples cos(th . m) are divided by prod_d (2 + cos th_d) / 3."""
+    import oracle
+    ns = (8, 6, 10)
+    k = np.array([1, 2, 3])
+    th = 2 * np.pi * k / np.array(ns)
+    m = np.stack(np.meshgrid(*[np.arange(n) for n in ns], indexing="ij"), -1)
+    f = np.cos((m * th).sum(-1))[..., None]
+    c = oracle.prefilter(f)
+    want = f / np.prod((2 + np.cos(th)) / 3)
+    assert np.abs(c - want).max() < 1e-12

@@ -81,6 +81,22 @@ def test_inference_forward_matches_quantised_reference(spo_lib, spec, P, grid_sc
     assert np.array_equal(v, got[:, 0].astype(np.float32))
 
 
+@pytest.mark.parametrize("P", [1, 129, 152 * 128 + 1])
+def test_fused_tile_sizing_edges(spo_lib, P):
+    """One position; one more than a tile; one more than a full wave of
+    128-position tiles on 152 SMs (two waves of 65-position tiles)."""
+    t = torch()
+    p = S.as_float32(S.init_params(FULL, seed=32, grid_scale=0.05))
+    pos = inputs.uniform_positions(P, 33)
+    ref, _ = S.forward(S.quantised(p), pos.astype(np.float64), act_round=S.round_bf16)
+    with load(spo_lib, FULL, p) as s:
+        got = s.eval(t.from_numpy(pos).cuda(), precision=1).cpu().numpy().astype(np.float64)
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    err = channel_errors(got, ref)
+    assert max(err) < 4e-3, err
+
+
 @pytest.mark.parametrize("given", [True, False])
 def test_gradients_match_reference(spo_lib, given):
     t = torch()
