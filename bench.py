@@ -529,6 +529,7 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
     res["crowd"] = measure_crowd(args, kind, steps)
     if cfg.N == 384:
         res["surrogate"] = measure_surrogate(cfg, s32, pos, steps)
+    res["prefilter"] = measure_prefilter(cfg)
     n32 = inputs.NIO32
     c = n32.make_coefs(np.float32)
     p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
@@ -541,6 +542,34 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
             res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
                                        "ms_per_step": round(step_ms, 5), "algo": a}
     return res
+
+
+def measure_prefilter(cfg):
+    """spo_prefilter on the workload's samples in FP64 ([nx, ny, nz, N]):
+    interpolating coefficients, three recursive passes in place."""
+    import torch
+    from paper_1708_02645_gb300 import spo
+    d = torch.from_numpy(cfg.make_coefs(np.float64)).cuda()
+    work = d.clone()
+    for _ in range(2):
+        work.copy_(d)
+        spo.prefilter(work)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps, ms = 3, 0.0
+    for _ in range(reps):
+        work.copy_(d)
+        e0.record()
+        spo.prefilter(work)
+        e1.record()
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+    ms /= reps
+    nbytes = d.numel() * 8
+    return {"ms": round(ms, 4), "table_bytes_f64": nbytes,
+            "gbs_per_pass": round(2 * nbytes / (ms / 3 * 1e-3) / 1e9, 1),
+            "what": "FP64 samples [64,64,64,384] -> interpolating B-spline coefficients "
+                    "(3 axis passes, each reading and writing the table at least once)"}
 
 
 def measure_surrogate(cfg, teacher, pos, steps):
