@@ -290,6 +290,18 @@ spo_status spo_eval_batch(const spo_set *const *sets, int nsets, const spo_work 
                           spo_kind kind, void *stream);
 
 /*
+ * Failure-path self-test.  Every device-side wait in the kernels (TMA and
+ * bulk copies, tensor-core MMAs) is bounded (2 s of %globaltimer); on giving
+ * up a kernel sets bit 0 of the device status word, drains what it issued
+ * and returns, and spo_device_status reports it.  spo_selftest_wait(limit_ns,
+ * stream, &timed_out) runs that path on purpose and harmlessly: a one-warp
+ * probe waits, through the same routine, on an mbarrier nothing arrives on,
+ * for limit_ns (at most 1 s), then the word is read and cleared; timed_out
+ * = 1 means the time-out was detected and reported.  Synchronous.
+ */
+spo_status spo_selftest_wait(uint64_t limit_ns, void *stream, int *timed_out);
+
+/*
  * Interpolating coefficients.  The table spo_create takes holds B-spline
  * coefficients; grid samples f(m / n) used as coefficients give a smoothed
  * f that does not pass through the samples.  spo_prefilter turns samples

@@ -57,6 +57,7 @@ SIGNATURES = [
     ("spo_get_param", _INT, [_P, _INT, ctypes.POINTER(_I64)]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
+    ("spo_selftest_wait", _INT, [ctypes.c_uint64, _P, ctypes.POINTER(_INT)]),
     ("spo_prefilter", _INT, [_P, _I64, _P, _INT, _P]),
     ("spo_surrogate_create", _INT, [_P, ctypes.c_uint64, ctypes.POINTER(_P)]),
     ("spo_surrogate_train", _INT, [_P, _P, _I64, _I64, ctypes.c_float, _P, ctypes.c_uint64, _P,
@@ -389,6 +390,15 @@ class OrbitalSet:
 class _Work(ctypes.Structure):
     _fields_ = [("set", ctypes.c_int32), ("reserved", ctypes.c_int32), ("P", ctypes.c_int64),
                 ("pos", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+
+
+def selftest_wait(limit_ns: int = 50_000_000, stream=None) -> bool:
+    """Run a bounded device-side wait that cannot succeed; True when the
+    time-out was detected and reported through the device status word."""
+    t = ctypes.c_int()
+    _check(load().spo_selftest_wait(int(limit_ns), _stream_handle(stream), ctypes.byref(t)),
+           "spo_selftest_wait")
+    return bool(t.value)
 
 
 def prefilter(samples, stream=None):
