@@ -408,6 +408,8 @@ struct spo_surrogate {
     int num_sms = 0;
     spo_detail::SurrImagePlan plan{};   // its weight image
     uint8_t *wimg = nullptr;
+    uint8_t *feat = nullptr;            // its encoded-feature images (grown on demand)
+    size_t feat_cap = 0;
 };
 
 namespace {
@@ -725,6 +727,7 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     free_scratch(s);
     cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
     cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
+    cudaFree(s->feat);
     delete s;
     return SPO_OK;
 }
@@ -771,9 +774,22 @@ spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos,
     if (precision != 0 && precision != 1) return fail(SPO_EINVAL, "precision must be 0 or 1");
     DeviceGuard guard(s->device);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (precision == 1 && s->use_tc) {   // one fused launch, no scratch
+    if (precision == 1 && s->use_tc) {   // encoding kernel + one fused launch
+        const bool vo = kind == SPO_KIND_V;
+        const size_t need = spo_detail::surrogate_feature_bytes(P, vo, s->num_sms);
+        if (need > s->feat_cap) {
+            cudaStreamSynchronize(st);   // the old buffer may still be read
+            cudaFree(s->feat);
+            s->feat = nullptr;
+            s->feat_cap = 0;
+            if (cudaMalloc(&s->feat, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(SPO_ENOMEM, "feature buffer of %zu bytes", need);
+            }
+            s->feat_cap = need;
+        }
         const cudaError_t e = spo_detail::surrogate_fused_tc(mlp_view(s), s->wimg, s->plan, s->grid16, s->lv, pos,
-                                                             P, out, kind == SPO_KIND_V, s->num_sms, st);
+                                                             P, out, vo, s->num_sms, s->feat, st);
         return e == cudaSuccess ? SPO_OK : cuda_fail(e, "fused surrogate evaluation");
     }
     // evaluate in chunks of at most 65536 positions (bounded scratch)

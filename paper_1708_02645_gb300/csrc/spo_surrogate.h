@@ -58,8 +58,13 @@ cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &pla
 // Fused inference on the tcgen05 tensor cores: encoding of pos [P][3] with
 // the FP16 grid ([levels][table][2]), BF16 layer inputs, FP32 accumulation;
 // out is [P][5][N] FP32, or [P][N] (value channel only) when values_only.
+// The encoding runs first as its own kernel, writing per tile the images of
+// the first layer's operands into feat (surrogate_feature_bytes(P, ...)
+// bytes); the fused kernel copies them in.
+size_t surrogate_feature_bytes(int64_t P, bool values_only, int num_sms);
 cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const SurrImagePlan &plan,
                                const __half *grid, const SurrLevels &lv, const float *pos, int64_t P,
-                               float *out, bool values_only, int num_sms, cudaStream_t stream);
+                               float *out, bool values_only, int num_sms, uint8_t *feat,
+                               cudaStream_t stream);
 
 }  // namespace spo_detail

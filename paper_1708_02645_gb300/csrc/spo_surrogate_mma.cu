@@ -69,6 +69,7 @@ struct FusedArgs {
     int N;                 // outputs (multiple of 16, <= 384)
     int nch;               // channels carried: 5 (VGL) or 1 (V)
     int tile_pos;          // positions per tile (<= 128; the remaining MMA rows idle)
+    const uint8_t *feat;   // encoded features: per (tile, channel) the 16 KB image of K-block 0
     float *out;
     unsigned int *status;
 };
@@ -101,60 +102,42 @@ __device__ __forceinline__ void store_h8(uint8_t *H, int ch, int row, int k, con
         make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
 }
 
-// Encoded features of the tile's positions into K-block 0 of H[c], c < nch
-// (rows tile_pos .. 127 are not written: their MMA rows are never stored).
-// Items (row, level) go four per thread and pass: all 32 corner gathers of
-// a pass are issued before any is used.
-__device__ void encode_tile(const FusedArgs &a, uint8_t *H, int64_t tile) {
-    const int L = a.lv.levels;
-    const int nitems = a.tile_pos * L;
-    for (int base = threadIdx.x; base < nitems; base += 4 * kThreads) {
-        __half2 th[4][8];
-        float tt[4][3];
+// Encoded features of every position, written as the shared-memory images
+// the fused kernel copies into K-block 0 of H[c]: per (tile, channel) 128
+// rows of 128 bytes in the 128-byte swizzle layout, row = position within the
+// tile, columns 2 l, 2 l + 1 = level l's two features (BF16).  One thread per
+// (position, level); rows tile_pos .. 127 and columns >= 2 levels are never
+// written (their MMA rows are never stored, their columns never read).
+__global__ void encode_image_kernel(const __half2 *__restrict__ grid, SurrLevels lv, const float *__restrict__ pos,
+                                    int64_t P, int tile_pos, int nch, uint8_t *__restrict__ img) {
+    const int L = lv.levels;
+    for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
+         it += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = it / L;
+        const int l = (int)(it - p * L);
+        const int64_t tile = p / tile_pos;
+        const int row = (int)(p - tile * tile_pos);
+        const float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
+        uint32_t slot[8];
+        float cw[5][8];
+        level_corners(r, lv.R[l], lv.dense[l] != 0, lv.mask, slot, cw);
+        const __half2 *g = grid + (size_t)l * lv.table;
+        float acc[5][2] = {};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int item = base + k * kThreads;
-            const int row = item / L, l = item - row * L;
-            const int64_t p = tile * a.tile_pos + row;
-            if (item < nitems && p < a.P) {
-                int c[3];
+        for (int q = 0; q < 8; ++q) {
+            const float2 th = __half22float2(g[slot[q]]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) level_axis(__ldg(a.pos + 3 * p + d), a.lv.R[l], c[d], tt[k][d]);
-                uint32_t slot[8];
-                corner_slots(c, a.lv.R[l], a.lv.dense[l] != 0, a.lv.mask, slot);
-                const __half2 *g = a.grid + (size_t)l * a.lv.table;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) th[k][q] = g[slot[q]];
-            } else {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) th[k][q] = __float2half2_rn(0.0f);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) tt[k][d] = 0.0f;
+            for (int ch = 0; ch < 5; ++ch) {
+                acc[ch][0] = fmaf(cw[ch][q], th.x, acc[ch][0]);
+                acc[ch][1] = fmaf(cw[ch][q], th.y, acc[ch][1]);
             }
         }
+        uint8_t *base = img + (size_t)tile * nch * kBlock;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int item = base + k * kThreads;
-            if (item >= nitems) break;
-            const int row = item / L, l = item - row * L;
-            float cw[5][8];
-            corner_weights(tt[k], a.lv.R[l], cw);
-            float acc[5][2] = {};
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const float2 v = __half22float2(th[k][q]);
-#pragma unroll
-                for (int ch = 0; ch < 5; ++ch) {
-                    acc[ch][0] = fmaf(cw[ch][q], v.x, acc[ch][0]);
-                    acc[ch][1] = fmaf(cw[ch][q], v.y, acc[ch][1]);
-                }
-            }
-#pragma unroll
-            for (int ch = 0; ch < 5; ++ch)
-                if (ch < a.nch)
-                    *reinterpret_cast<uint32_t *>(H + (uint32_t)ch * kChan + sw128_offset(row, 2 * l)) =
-                        pack_bf16(acc[ch][0], acc[ch][1]);
-        }
+        for (int ch = 0; ch < 5; ++ch)
+            if (ch < nch)
+                *reinterpret_cast<uint32_t *>(base + (uint32_t)ch * kBlock + sw128_offset(row, 2 * l)) =
+                    pack_bf16(acc[ch][0], acc[ch][1]);
     }
 }
 
@@ -167,6 +150,7 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
     const uint32_t full_bar = s0 + kOffBar;   // two barriers, 8 bytes apart
     const uint32_t mma_bar = s0 + kOffBar + 16;
     const uint32_t slot = s0 + kOffBar + 24;
+    const uint32_t feat_bar = s0 + kOffBar + 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool leader = threadIdx.x == 0;
 
@@ -187,6 +171,7 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
         mbar_init(full_bar, 1);
         mbar_init(full_bar + 8, 1);
         mbar_init(mma_bar, 1);
+        mbar_init(feat_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before_sync();
@@ -195,6 +180,19 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(sm + kOffBar + 24);
     if (leader)
         while (issued < total_loads && issued < 2) issue_load(issued++);
+    // leader: copy a tile's encoded features into K-block 0 of H[c]
+    auto issue_features = [&](int64_t tile) {
+        const uint32_t bytes = (uint32_t)a.nch * kBlock;
+        mbar_arrive_expect_tx(feat_bar, bytes);
+        for (int c = 0; c < a.nch; ++c)
+            bulk_load(sH + (uint32_t)c * kChan, a.feat + ((size_t)tile * a.nch + c) * kBlock, kBlock, feat_bar);
+    };
+    uint32_t feat_phase = 0;
+    bool feat_pending = false;   // leader: a feature copy is in flight
+    if (leader && blockIdx.x < ntiles) {
+        issue_features(blockIdx.x);
+        feat_pending = true;
+    }
 
     const int wq = warp & 3, grp = warp >> 2;         // lane quarter, group within it
     const uint32_t lane_addr = tmem + ((uint32_t)(32 * wq) << 16);
@@ -223,10 +221,12 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
 
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x, ++it) {
-        encode_tile(a, H, tile);
-        fence_proxy_async_smem();
-        tc_fence_before_sync();
-        __syncthreads();
+        {   // this tile's features (copy issued at the end of the previous tile)
+            const bool ok = mbar_wait_bounded(feat_bar, feat_phase);
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            feat_phase ^= 1u;
+            if (leader) feat_pending = false;
+        }
 
         for (int l = 0; l < a.nl && !failed; ++l) {
             const uint64_t g0 = (uint64_t)it * (uint64_t)a.nloads + (uint64_t)l;
@@ -351,6 +351,11 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
                     }
                     if (!wait_mma(bad)) { failed = true; break; }
                     if (leader) release(g);
+                    if (leader && n0 + kChunk >= a.N && tile + gridDim.x < ntiles) {
+                        // H is no longer read: bring in the next tile's features
+                        issue_features(tile + gridDim.x);
+                        feat_pending = true;
+                    }
                     const int subs = nn / 16;
                     for (int i = grp; i < a.nch * subs; i += 4) {
                         const int c = i / subs, s = i - c * subs;
@@ -379,6 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
             atomicOr(a.status, 1u);
             // let the weight copies in flight land (bounded) before the memory goes away
             for (uint64_t g = consumed; g < issued; ++g) weights_ready(g);
+            if (feat_pending) mbar_wait_bounded(feat_bar, feat_phase);
         }
         mbar_wait_bounded(mma_bar, mma_phase ^ 1u);   // the phase that was being waited for
         tc_fence_before_sync();
@@ -480,9 +486,19 @@ cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &pla
     return cudaGetLastError();
 }
 
+size_t surrogate_feature_bytes(int64_t P, bool values_only, int num_sms) {
+    const int sms = num_sms > 0 ? num_sms : 148;
+    const int64_t waves = (P + (int64_t)kTile * sms - 1) / ((int64_t)kTile * sms);
+    const int64_t tiles_wanted = waves * sms;
+    const int64_t tile_pos = std::max<int64_t>(1, (P + tiles_wanted - 1) / tiles_wanted);
+    const int64_t ntiles = (P + tile_pos - 1) / tile_pos;
+    return (size_t)ntiles * (values_only ? 1 : 5) * kBlock;
+}
+
 cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const SurrImagePlan &plan,
                                const __half *grid, const SurrLevels &lv, const float *pos, int64_t P,
-                               float *out, bool values_only, int num_sms, cudaStream_t stream) {
+                               float *out, bool values_only, int num_sms, uint8_t *feat,
+                               cudaStream_t stream) {
     if (P <= 0) return cudaSuccess;
     FusedArgs a{};
     a.grid = reinterpret_cast<const __half2 *>(grid);
@@ -513,6 +529,14 @@ cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const S
     a.tile_pos = (int)std::max<int64_t>(1, (P + tiles_wanted - 1) / tiles_wanted);
     const int64_t ntiles = (P + a.tile_pos - 1) / a.tile_pos;
     const int grid_x = (int)std::min<int64_t>(ntiles, sms);
+    a.feat = feat;
+    {
+        const int64_t items = P * lv.levels;
+        const int blocks = (int)std::min<int64_t>((items + 255) / 256, (int64_t)sms * 16);
+        encode_image_kernel<<<blocks, 256, 0, stream>>>(a.grid, lv, pos, P, a.tile_pos, a.nch, feat);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     surrogate_fused_kernel<<<grid_x, kThreads, kSmemBytes, stream>>>(a);
     return cudaGetLastError();
 }
