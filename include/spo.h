@@ -321,7 +321,7 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  * Learned surrogate — a small learned function of the position standing in
  * for the B-spline table, aimed at the memory footprint the paper attacks
  * (Sec. 6.3-6.4: memory per walker and up to 3.8x smaller runs); the
- * B-spline stays its teacher and the judge of its error.  The paper has no
+ * B-spline stays its teacher and the arbiter of its error.  The paper has no
  * such surrogate; this is one of the patterns built on the path.
  *
  * Function: a periodic multiresolution hashed grid (levels l with

@@ -4,8 +4,8 @@ The surrogate replaces the B-spline table by a small learned function of
 the position: a periodic multiresolution hashed grid of features followed by
 a multilayer perceptron whose outputs are the N orbitals.  It aims at the
 memory footprint the paper attacks (arXiv 1708.02645, Sec. 6.3 and the
-memory results of Sec. 6.4, up to 3.8x smaller); the B-spline stays its
-judge.  The paper has no such surrogate, so this file fixes the function
+memory results of Sec. 6.4, up to 3.8x smaller); the B-spline stays the
+arbiter of its error.  The paper has no such surrogate, so this file fixes the function
 the GPU kernels must compute:
 
 * levels l = 0..L-1 with resolutions R_l = floor(R_min * b^l), b =
