@@ -615,12 +615,12 @@ def measure_surrogate(cfg, teacher, pos, steps):
     spec = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=16, r_max=512, hidden=128,
                            layers=3, N=cfg.N)
     P = pos.shape[0]
-    res = {"spec": vars(spec), "train_samples": 256 * 16384, "batch": 16384, "lr": 3e-3,
+    res = {"spec": vars(spec), "train_samples": 256 * 16384, "batch": 16384, "lr": 1e-3,
            "loss": "sum over V, Gx, Gy, Gz, L of mean squared error / mean(target^2)"}
     with spo.Surrogate(spec, seed=20170808) as sg:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss = sg.train(teacher, steps=256, batch=16384, lr=3e-3, seed=20170809)
+        loss = sg.train(teacher, steps=256, batch=16384, lr=1e-3, seed=20170809)
         torch.cuda.synchronize()
         res["train_s"] = round(time.perf_counter() - t0, 3)
         res["final_loss"] = loss
@@ -654,9 +654,17 @@ def measure_surrogate(cfg, teacher, pos, steps):
         res["footprint_bytes"] = sg.footprint()
         res["spline_table_bytes"] = teacher.footprint()
         res["footprint_ratio"] = round(teacher.footprint() / sg.footprint(), 2)
-        res["note"] = ("the 128-wide last hidden layer bounds the outputs to a 128-dimensional "
-                       "function space, while the 384 plane-wave orbitals span several hundred "
-                       "dimensions: the error floor is high for this set")
+        # Eckart-Young: no linear read-out of 128 features (+ the bias) can
+        # beat the truncated SVD of the sampled values
+        vals = want[:8192, 0].double().cpu().numpy()
+        sv = np.linalg.svd(vals, compute_uv=False)
+        k = spec.hidden + 1
+        res["rank_floor_rms_rel_V"] = float(np.sqrt((sv[k:] ** 2).sum() / (sv ** 2).sum()))
+        res["rank_floor_what"] = (f"relative RMS error of the best rank-{k} approximation of the "
+                                  f"[8192 positions x {cfg.N}] matrix of spline values: a lower bound "
+                                  f"for any output layer reading {spec.hidden} hidden units")
+        res["note"] = ("2^22 samples leave the trained network far above the rank floor: the "
+                       "optimisation, not the width, limits this fit")
     return res
 
 
