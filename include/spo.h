@@ -353,8 +353,9 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  *   parameter for P device positions [P][3] and device targets [P][5][N]
  *   (same channel weights rule), written to host arrays laid out as in
  *   spo_surrogate_params.  Leaves the parameters unchanged; synchronous.
- * spo_surrogate_set_optimizer(s, beta1, beta2, eps): Adam's moment decay
- *   rates and denominator guard (defaults 0.9, 0.99, 1e-15).
+ * spo_surrogate_set_optimizer(s, beta1, beta2, eps, grid_lr_mult): Adam's
+ *   moment decay rates and denominator guard (defaults 0.9, 0.99, 1e-15),
+ *   and the grid's learning rate as a multiple of `lr` (default 1).
  * spo_surrogate_nparams(s, &n) / spo_surrogate_state(s, params, m, v, &step,
  *   restore): the training state for checkpoints: all FP32 master parameters
  *   laid out [grid | W0 | b0 | W1 | b1 | ...] (n floats), Adam's first and
@@ -383,7 +384,8 @@ spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos,
 spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *target, int64_t P,
                               const float *channel_weights, float *loss, float *grid, float *const *W,
                               float *const *b, void *stream);
-spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps);
+spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps,
+                                       float grid_lr_mult);
 spo_status spo_surrogate_nparams(const spo_surrogate *s, int64_t *n);
 spo_status spo_surrogate_state(spo_surrogate *s, float *params, float *m, float *v, int64_t *step,
                                int restore);

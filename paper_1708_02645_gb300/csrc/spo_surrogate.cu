@@ -389,6 +389,7 @@ struct spo_surrogate {
     int64_t w_off[kMaxLayers] = {}, b_off[kMaxLayers] = {};
     int64_t adam_t = 0;
     float beta1 = 0.9f, beta2 = 0.99f, eps = 1e-15f;
+    float grid_lr_mult = 1.0f;   // the grid's learning rate relative to the perceptron's
 
     // inference copies
     __half *grid16 = nullptr;
@@ -870,8 +871,14 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
             const float b1 = s->beta1, b2 = s->beta2;
             const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->adam_t));
             const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->adam_t));
-            adam_kernel<<<blocks_for(s->nparam), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->nparam,
-                                                               lr, b1, b2, s->eps, c1, c2);
+            // the grid (the first grid_n parameters) and the perceptron may
+            // take different rates
+            adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n,
+                                                               lr * s->grid_lr_mult, b1, b2, s->eps, c1, c2);
+            const int64_t nm = s->nparam - s->grid_n;
+            adam_kernel<<<blocks_for(nm), 256, 0, st>>>(s->param + s->grid_n, s->grad + s->grid_n,
+                                                        s->m1 + s->grid_n, s->m2 + s->grid_n, nm, lr, b1, b2,
+                                                        s->eps, c1, c2);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess && step == steps - 1) {
@@ -887,14 +894,17 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
     return e == cudaSuccess ? SPO_OK : cuda_fail(e, "surrogate training");
 }
 
-spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps) {
+spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps,
+                                       float grid_lr_mult) {
     fail(SPO_OK, "");
     if (!s) return fail(SPO_EINVAL, "surrogate is NULL");
-    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
-        return fail(SPO_EINVAL, "need 0 <= beta1, beta2 < 1 and eps > 0");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f) ||
+        !(grid_lr_mult > 0.0f))
+        return fail(SPO_EINVAL, "need 0 <= beta1, beta2 < 1, eps > 0 and grid_lr_mult > 0");
     s->beta1 = beta1;
     s->beta2 = beta2;
     s->eps = eps;
+    s->grid_lr_mult = grid_lr_mult;
     return SPO_OK;
 }
 

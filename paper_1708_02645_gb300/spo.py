@@ -65,7 +65,8 @@ SIGNATURES = [
     ("spo_surrogate_eval", _INT, [_P, _INT, _P, _I64, _P, _INT, _P]),
     ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_float), _P, _P, _P,
                                   _P]),
-    ("spo_surrogate_set_optimizer", _INT, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    ("spo_surrogate_set_optimizer", _INT, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                           ctypes.c_float]),
     ("spo_surrogate_nparams", _INT, [_P, ctypes.POINTER(_I64)]),
     ("spo_surrogate_state", _INT, [_P, _P, _P, _P, ctypes.POINTER(_I64), _INT]),
     ("spo_surrogate_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
@@ -595,9 +596,9 @@ class Surrogate:
         _check(load().spo_surrogate_footprint(self._h, ctypes.byref(n)), "spo_surrogate_footprint")
         return int(n.value)
 
-    def set_optimizer(self, beta1=0.9, beta2=0.99, eps=1e-15):
-        _check(load().spo_surrogate_set_optimizer(self._h, float(beta1), float(beta2), float(eps)),
-               "spo_surrogate_set_optimizer")
+    def set_optimizer(self, beta1=0.9, beta2=0.99, eps=1e-15, grid_lr_mult=1.0):
+        _check(load().spo_surrogate_set_optimizer(self._h, float(beta1), float(beta2), float(eps),
+                                                  float(grid_lr_mult)), "spo_surrogate_set_optimizer")
 
     def state(self):
         """(params, m, v, step): the FP32 training state."""
