@@ -191,6 +191,102 @@ gemm_kernel(const float *__restrict__ A, const void *__restrict__ Bv, float *__r
     }
 }
 
+// The same three products with 128 x 64 CTA tiles, 8 x 4 outputs per thread,
+// 16-byte global and shared-memory accesses and packed FP32x2 FMA; used when
+// every row length and leading dimension is a multiple of 4 floats and the
+// pointers are 16-byte aligned (the scalar kernel above takes the rest).
+constexpr int VM = 128, VN = 64, VK = 16;
+
+__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+
+template <int MODE>
+__global__ void __launch_bounds__(256)
+gemm_v4_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C,
+               const float *__restrict__ bias, int M, int N, int K, int lda, int ldb, int k_chunk) {
+    __shared__ __align__(16) float As[VK][VM + 4];
+    __shared__ __align__(16) float Bs[VK][VN + 4];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;   // columns tx*4 .. +3, rows ty*8 .. +7
+    const int i0 = blockIdx.x * VM, j0 = blockIdx.y * VN;
+    const int kbeg = blockIdx.z * k_chunk, kend = min(K, kbeg + k_chunk);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 acc[8][2];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u][0] = acc[u][1] = make_float2(0.f, 0.f);
+    for (int k0 = kbeg; k0 < kend; k0 += VK) {
+        if (MODE == 2) {   // A[k][i]: rows along i
+            for (int e = tid; e < VK * VM / 4; e += 256) {
+                const int kk = e / (VM / 4), iq = e - kk * (VM / 4);
+                const int k = k0 + kk, i = i0 + 4 * iq;
+                const float4 v = (k < kend && i < M) ? ldg4(A + (int64_t)k * lda + i) : zero;
+                *reinterpret_cast<float4 *>(&As[kk][4 * iq]) = v;
+            }
+        } else {           // A[i][k]: rows along k, stored transposed
+            for (int e = tid; e < VM * VK / 4; e += 256) {
+                const int ii = e / (VK / 4), kq = e - ii * (VK / 4);
+                const int i = i0 + ii, k = k0 + 4 * kq;
+                const float4 v = (i < M && k < kend) ? ldg4(A + (int64_t)i * lda + k) : zero;
+                As[4 * kq + 0][ii] = v.x;
+                As[4 * kq + 1][ii] = v.y;
+                As[4 * kq + 2][ii] = v.z;
+                As[4 * kq + 3][ii] = v.w;
+            }
+        }
+        if (MODE == 0) {   // B[j][k]: rows along k, stored transposed
+            for (int e = tid; e < VN * VK / 4; e += 256) {
+                const int jj = e / (VK / 4), kq = e - jj * (VK / 4);
+                const int j = j0 + jj, k = k0 + 4 * kq;
+                const float4 v = (j < N && k < kend) ? ldg4(B + (int64_t)j * ldb + k) : zero;
+                Bs[4 * kq + 0][jj] = v.x;
+                Bs[4 * kq + 1][jj] = v.y;
+                Bs[4 * kq + 2][jj] = v.z;
+                Bs[4 * kq + 3][jj] = v.w;
+            }
+        } else {           // B[k][j]: rows along j
+            for (int e = tid; e < VK * VN / 4; e += 256) {
+                const int kk = e / (VN / 4), jq = e - kk * (VN / 4);
+                const int k = k0 + kk, j = j0 + 4 * jq;
+                const float4 v = (k < kend && j < N) ? ldg4(B + (int64_t)k * ldb + j) : zero;
+                *reinterpret_cast<float4 *>(&Bs[kk][4 * jq]) = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < VK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][8 * ty]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][8 * ty + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][4 * tx]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 au = make_float2(a[u], a[u]);
+                acc[u][0] = __ffma2_rn(au, b01, acc[u][0]);
+                acc[u][1] = __ffma2_rn(au, b23, acc[u][1]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + 8 * ty + u;
+        if (i >= M) continue;
+        const float r[4] = {acc[u][0].x, acc[u][0].y, acc[u][1].x, acc[u][1].y};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = j0 + 4 * tx + v;
+            if (j >= N) continue;
+            if (MODE == 2) {
+                atomicAdd(C + (int64_t)i * N + j, r[v]);
+            } else {
+                float x = r[v];
+                if (MODE == 0 && bias && i % 5 == 0) x += __ldg(bias + j);
+                C[(int64_t)i * N + j] = x;
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // softplus with channels
 // ---------------------------------------------------------------------------
@@ -446,8 +542,31 @@ spo_status grow_scratch(spo_surrogate *s, int64_t P) {
     return SPO_OK;
 }
 
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 cudaError_t gemm(int mode, bool bf16, const float *A, const void *B, float *C, const float *bias, int M,
                  int N, int K, int lda, int ldb, cudaStream_t st) {
+    // vector forms: every row that is read four floats at a time is a
+    // multiple of 4 long and starts 16-byte aligned
+    const bool vec = !bf16 && aligned16(A) && aligned16(B) && lda % 4 == 0 && ldb % 4 == 0 &&
+                     (mode == 2 ? (M % 4 == 0 && N % 4 == 0) : (K % 4 == 0 && (mode == 0 || N % 4 == 0)));
+    if (vec) {
+        const float *Bf = static_cast<const float *>(B);
+        if (mode == 2) {
+            const int tiles = ((M + VM - 1) / VM) * ((N + VN - 1) / VN);
+            const int chunks = std::max(1, std::min(std::max(1, K / 256), (4 * 152 + tiles - 1) / tiles));
+            const int k_chunk = ((K + chunks - 1) / chunks + VK - 1) / VK * VK;
+            dim3 g((M + VM - 1) / VM, (N + VN - 1) / VN, (K + k_chunk - 1) / k_chunk);
+            gemm_v4_kernel<2><<<g, 256, 0, st>>>(A, Bf, C, bias, M, N, K, lda, ldb, k_chunk);
+        } else {
+            dim3 g((M + VM - 1) / VM, (N + VN - 1) / VN, 1);
+            if (mode == 0)
+                gemm_v4_kernel<0><<<g, 256, 0, st>>>(A, Bf, C, bias, M, N, K, lda, ldb, K);
+            else
+                gemm_v4_kernel<1><<<g, 256, 0, st>>>(A, Bf, C, bias, M, N, K, lda, ldb, K);
+        }
+        return cudaGetLastError();
+    }
     if (mode == 2) {
         // C[M][N] += sum over the K rows of the activations: split that range
         // across CTAs so that about four CTAs per SM run (152 SMs)
