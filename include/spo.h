@@ -363,6 +363,9 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  *   or from (restore != 0) host arrays.  Restoring refreshes the inference
  *   copies.  Synchronous.
  * spo_surrogate_footprint(s, &bytes): device bytes of the inference copies.
+ * Calls on one surrogate must be ordered (one stream): they share its
+ * scratch (the encoded-feature images of precision 1 grow with P and stay
+ * allocated until spo_surrogate_destroy).
  * spo_surrogate_params(s, grid, W, b, to_device): copy all FP32 master
  *   parameters from (to_device != 0) or to host arrays: grid
  *   [levels][2^log2_table][features]; W[l] [out][in]; b[l] [out]
