@@ -981,8 +981,13 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
     for (int64_t step = 0; step < steps && e == cudaSuccess; ++step) {
         sample_kernel<<<blocks_for(3 * P), 256, 0, st>>>(s->pos, 3 * P, seed,
                                                            (unsigned long long)step * 3 * P);
-        spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->pos, P, s->target, st, SPO_ALGO_AUTO);
-        if (es != SPO_OK) return es;
+        const spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->pos, P, s->target, st,
+                                                     SPO_ALGO_AUTO);
+        if (es != SPO_OK) {   // keep the inference copies in step with the parameters taken so far
+            refresh_inference(s, st);
+            cudaStreamSynchronize(st);
+            return es;
+        }
         if (step == 0) e = channel_weights_for(s, s->target, P, channel_weights, cw, st);
         if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st);
         if (e == cudaSuccess) {
