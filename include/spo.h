@@ -348,11 +348,17 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  *   VGL; precision 0 evaluates the FP32 master parameters (CUDA cores),
  *   precision 1 the inference copies (FP16 grid, BF16 weights and
  *   activations, FP32 accumulation on the tcgen05 tensor cores).
- * spo_surrogate_grad(s, pos, target, P, channel_weights, &loss, grid, W, b,
- *   stream): loss and its gradient with respect to every FP32 master
- *   parameter for P device positions [P][3] and device targets [P][5][N]
- *   (same channel weights rule), written to host arrays laid out as in
- *   spo_surrogate_params.  Leaves the parameters unchanged; synchronous.
+ * spo_surrogate_grad(s, pos, target, P, channel_weights, precision, &loss,
+ *   grid, W, b, stream): loss and its gradient with respect to every FP32
+ *   master parameter for P device positions [P][3] and device targets
+ *   [P][5][N] (same channel weights rule), written to host arrays laid out
+ *   as in spo_surrogate_params; precision 0 computes every product in FP32
+ *   on the CUDA cores, 1 as training does on the tensor cores (the operands
+ *   of the forward, weight-gradient and data-gradient products rounded to
+ *   BF16, FP32 accumulation).  Leaves the parameters unchanged; synchronous.
+ * spo_surrogate_set_train_precision(s, precision): 1 (default) trains with
+ *   the layers' products on the tcgen05 tensor cores as above, 0 in FP32 on
+ *   the CUDA cores.
  * spo_surrogate_set_optimizer(s, beta1, beta2, eps, grid_lr_mult): Adam's
  *   moment decay rates and denominator guard (defaults 0.9, 0.99, 1e-15),
  *   and the grid's learning rate as a multiple of `lr` (default 1).
@@ -385,8 +391,9 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
 spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos, int64_t P,
                               float *out, int precision, void *stream);
 spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *target, int64_t P,
-                              const float *channel_weights, float *loss, float *grid, float *const *W,
-                              float *const *b, void *stream);
+                              const float *channel_weights, int precision, float *loss, float *grid,
+                              float *const *W, float *const *b, void *stream);
+spo_status spo_surrogate_set_train_precision(spo_surrogate *s, int precision);
 spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps,
                                        float grid_lr_mult);
 spo_status spo_surrogate_nparams(const spo_surrogate *s, int64_t *n);

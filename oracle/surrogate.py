@@ -156,10 +156,13 @@ def quantised(params: SurrogateParams) -> SurrogateParams:
                            [np.array(b) for b in params.b])
 
 
-def forward(params: SurrogateParams, pos, act_round=None):
+def forward(params: SurrogateParams, pos, act_round=None, gemm_round=None):
     """Surrogate outputs [P, 5, N] (V, Gx, Gy, Gz, L) and the intermediates.
     act_round, if given, is applied to every layer's input (all channels):
-    the inference precision rounds activations to bfloat16 there."""
+    the inference precision rounds activations to bfloat16 there.
+    gemm_round, if given, is applied to both operands of every layer's
+    product (input and weights), as the tensor-core training reads them; the
+    stored intermediates stay unrounded."""
     h, enc_cache = encode(params, pos)
     acts = [h]
     pre = []
@@ -167,7 +170,10 @@ def forward(params: SurrogateParams, pos, act_round=None):
     for l in range(nl):
         if act_round is not None:
             h = act_round(h)
-        z = np.einsum("pci,oi->pco", h, params.W[l])
+        if gemm_round is not None:
+            z = np.einsum("pci,oi->pco", gemm_round(h), gemm_round(params.W[l]))
+        else:
+            z = np.einsum("pci,oi->pco", h, params.W[l])
         z[:, 0, :] += params.b[l]
         pre.append(z)
         if l == nl - 1:
@@ -189,9 +195,12 @@ def loss(out, target, wch):
     return float(sum(wch[c] * np.mean(d[:, c] ** 2) for c in range(5)))
 
 
-def grads(params: SurrogateParams, pos, target, wch):
-    """Loss and its gradients with respect to the grid table, W and b."""
-    out, (acts, pre, enc_cache) = forward(params, pos)
+def grads(params: SurrogateParams, pos, target, wch, gemm_round=None):
+    """Loss and its gradients with respect to the grid table, W and b.
+    gemm_round, if given, rounds both operands of every product (forward,
+    weight gradient, data gradient): the tensor-core training reading."""
+    R = gemm_round if gemm_round is not None else (lambda x: x)
+    out, (acts, pre, enc_cache) = forward(params, pos, gemm_round=gemm_round)
     P, _, N = out.shape
     g = np.zeros_like(out)
     for c in range(5):
@@ -211,9 +220,9 @@ def grads(params: SurrogateParams, pos, target, wch):
                         + g[:, 4] * (d3 * g2 + d2 * z[:, 4]))
             gz[:, 1:4] = g[:, 1:4] * d1[:, None, :] + 2.0 * (g[:, 4] * d2)[:, None, :] * zd
             gz[:, 4] = g[:, 4] * d1
-        gW[l] = np.einsum("pco,pci->oi", gz, acts[l])
+        gW[l] = np.einsum("pco,pci->oi", R(gz), R(acts[l]))
         gb[l] = gz[:, 0].sum(0)
-        g = np.einsum("pco,oi->pci", gz, params.W[l])
+        g = np.einsum("pco,oi->pci", R(gz), R(params.W[l]))
     # g: gradient w.r.t. the encoded features [P, 5, levels * F]
     spec = params.spec
     gg = np.zeros_like(params.grid)

@@ -346,21 +346,21 @@ struct ChannelWeights {
 };
 
 // g = 2 w_c (out - target) / (P N) in FP32; the loss sum_c w_c mean(d^2)
-// is summed per thread in FP32, per block and across blocks in FP64.  Rows
-// (position, channel) go one per block iteration, orbitals across threads.
+// is summed per thread in FP32, per block and across blocks in FP64.
+// blockIdx.y is the channel c; blocks stride over positions, threads over
+// the orbitals of row (p, c).
 __global__ void loss_kernel(const float *__restrict__ out, const float *__restrict__ target, int64_t P,
                             int64_t N, ChannelWeights cw, float *__restrict__ g, double *loss) {
     __shared__ double red[256];
+    const int ch = blockIdx.y;
     const double inv = 1.0 / ((double)P * (double)N);
+    const float w = cw.w[ch], gs = (float)(2.0 * cw.w[ch] * inv);
     float local = 0.0f;
-    for (int64_t row = blockIdx.x; row < P * 5; row += gridDim.x) {
-        const int ch = (int)(row % 5);
-        const float w = cw.w[ch], gs = (float)(2.0 * cw.w[ch] * inv);
-        const float *o = out + row * N, *t = target + row * N;
-        float *gr = g + row * N;
+    for (int64_t p = blockIdx.x; p < P; p += gridDim.x) {
+        const int64_t base = (p * 5 + ch) * N;
         for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
-            const float d = o[j] - t[j];
-            gr[j] = gs * d;
+            const float d = out[base + j] - target[base + j];
+            g[base + j] = gs * d;
             local = fmaf(w * d, d, local);
         }
     }
@@ -410,19 +410,39 @@ __global__ void bias_grad_kernel(const float *__restrict__ gz, int64_t P, int W,
     atomicAdd(gb + j, s);
 }
 
+__device__ __forceinline__ void adam_one(float &p, float &g, float &m, float &v, float lr, float b1, float b2,
+                                         float eps, float c1, float c2) {
+    const float mi = b1 * m + (1.0f - b1) * g;
+    const float vi = b2 * v + (1.0f - b2) * g * g;
+    m = mi;
+    v = vi;
+    p -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    g = 0.0f;
+}
+
+// One Adam step over n parameters (the gradient is zeroed for the next
+// step); four per thread when the arrays are 16-byte aligned.
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
                             float c1, float c2) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float gi = g[i];
-        const float mi = b1 * m[i] + (1.0f - b1) * gi;
-        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
-        m[i] = mi;
-        v[i] = vi;
-        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-        g[i] = 0.0f;
+    const bool vec = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
+                       reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15u) == 0;
+    const int64_t n4 = vec ? n / 4 : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 P4 = reinterpret_cast<float4 *>(p)[i], G4 = reinterpret_cast<float4 *>(g)[i];
+        float4 M4 = reinterpret_cast<float4 *>(m)[i], V4 = reinterpret_cast<float4 *>(v)[i];
+        adam_one(P4.x, G4.x, M4.x, V4.x, lr, b1, b2, eps, c1, c2);
+        adam_one(P4.y, G4.y, M4.y, V4.y, lr, b1, b2, eps, c1, c2);
+        adam_one(P4.z, G4.z, M4.z, V4.z, lr, b1, b2, eps, c1, c2);
+        adam_one(P4.w, G4.w, M4.w, V4.w, lr, b1, b2, eps, c1, c2);
+        reinterpret_cast<float4 *>(p)[i] = P4;
+        reinterpret_cast<float4 *>(g)[i] = G4;
+        reinterpret_cast<float4 *>(m)[i] = M4;
+        reinterpret_cast<float4 *>(v)[i] = V4;
     }
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        adam_one(p[i], g[i], m[i], v[i], lr, b1, b2, eps, c1, c2);
 }
 
 // uniform positions in the unit cube, splitmix64 on (seed, counter)
@@ -507,6 +527,10 @@ struct spo_surrogate {
     uint8_t *wimg = nullptr;
     uint8_t *feat = nullptr;            // its encoded-feature images (grown on demand)
     size_t feat_cap = 0;
+
+    int train_precision = 1;            // 1: training GEMMs on the tensor cores (BF16), 0: FP32
+    uint8_t *img[2] = {nullptr, nullptr};   // GEMM operand images for the tensor-core training
+    size_t img_cap[2] = {0, 0};
 };
 
 namespace {
@@ -587,19 +611,77 @@ cudaError_t gemm(int mode, bool bf16, const float *A, const void *B, float *C, c
     return cudaGetLastError();
 }
 
-// Forward pass with the FP32 master parameters over P positions in s->pos
-// (or `pos`), leaving activations in s->act / s->pre; returns the output.
-cudaError_t forward_fp32(spo_surrogate *s, const float *pos, int64_t P, float *out, cudaStream_t st) {
+// Operand images for the tensor-core form of the three products of layer
+// l over M = 5 P rows: forward (X [M][in], W [o][in]), weight gradient
+// (gz^T, X^T: K = M) and data gradient (gz [M][o], W^T).
+cudaError_t ensure_images(spo_surrogate *s, int64_t M) {
+    size_t need[2] = {0, 0};
+    for (int l = 0; l < s->nl; ++l) {
+        const int64_t in = s->widths[l], o = s->widths[l + 1];
+        need[0] = std::max({need[0], spo_detail::bf16_image_bytes(M, in), spo_detail::bf16_image_bytes(o, M),
+                            spo_detail::bf16_image_bytes(M, o)});
+        need[1] = std::max({need[1], spo_detail::bf16_image_bytes(o, in), spo_detail::bf16_image_bytes(in, M),
+                            spo_detail::bf16_image_bytes(in, o)});
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (s->img_cap[k] >= need[k]) continue;
+        cudaFree(s->img[k]);
+        s->img[k] = nullptr;
+        s->img_cap[k] = 0;
+        const cudaError_t e = cudaMalloc(&s->img[k], need[k]);
+        if (e != cudaSuccess) return e;
+        s->img_cap[k] = need[k];
+    }
+    return cudaSuccess;
+}
+
+// Z [M][o] = X [M][in] W_l^T, plus b_l on the value rows
+cudaError_t lin_forward(spo_surrogate *s, bool tc, const float *X, int l, float *Z, int64_t M, cudaStream_t st) {
+    const int in = s->widths[l], o = s->widths[l + 1];
+    const float *W = s->param + s->w_off[l], *b = s->param + s->b_off[l];
+    if (!tc) return gemm(0, false, X, W, Z, b, (int)M, o, in, in, in, st);
+    cudaError_t e = spo_detail::to_bf16_image(X, M, in, in, false, s->img[0], st);
+    if (e == cudaSuccess) e = spo_detail::to_bf16_image(W, o, in, in, false, s->img[1], st);
+    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], M, o, in, Z, b, false, st);
+    return e;
+}
+
+// dW_l [o][in] += gz [M][o]^T X [M][in]
+cudaError_t lin_wgrad(spo_surrogate *s, bool tc, const float *gz, const float *X, int l, int64_t M,
+                      cudaStream_t st) {
+    const int in = s->widths[l], o = s->widths[l + 1];
+    float *dW = s->grad + s->w_off[l];
+    if (!tc) return gemm(2, false, gz, X, dW, nullptr, o, in, (int)M, o, in, st);
+    cudaError_t e = spo_detail::to_bf16_image(gz, M, o, o, true, s->img[0], st);
+    if (e == cudaSuccess) e = spo_detail::to_bf16_image(X, M, in, in, true, s->img[1], st);
+    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], o, in, M, dW, nullptr, true, st);
+    return e;
+}
+
+// G [M][in] = gz [M][o] W_l [o][in]
+cudaError_t lin_dgrad(spo_surrogate *s, bool tc, const float *gz, int l, float *G, int64_t M, cudaStream_t st) {
+    const int in = s->widths[l], o = s->widths[l + 1];
+    const float *W = s->param + s->w_off[l];
+    if (!tc) return gemm(1, false, gz, W, G, nullptr, (int)M, in, o, o, in, st);
+    cudaError_t e = spo_detail::to_bf16_image(gz, M, o, o, false, s->img[0], st);
+    if (e == cudaSuccess) e = spo_detail::to_bf16_image(W, o, in, in, true, s->img[1], st);
+    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], M, in, o, G, nullptr, false, st);
+    return e;
+}
+
+// Forward pass with the FP32 master parameters over P positions, leaving
+// activations in s->act / s->pre; the output goes to `out`.  tc: the
+// layers' products on the tensor cores (BF16 operands, FP32 accumulation).
+cudaError_t forward_train(spo_surrogate *s, const float *pos, int64_t P, float *out, cudaStream_t st, bool tc) {
     cudaError_t e;
     encode_fwd_kernel<float><<<blocks_for(P * s->lv.levels), 256, 0, st>>>(s->param, s->lv, pos, P,
                                                                              s->act[0]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int M = (int)(5 * P);
+    if (tc && (e = ensure_images(s, 5 * P)) != cudaSuccess) return e;
     for (int l = 0; l < s->nl; ++l) {
-        const int in = s->widths[l], o = s->widths[l + 1];
+        const int o = s->widths[l + 1];
         float *z = (l == s->nl - 1 && out) ? out : s->pre[l];
-        e = gemm(0, false, s->act[l], s->param + s->w_off[l], z, s->param + s->b_off[l], M, o, in, in,
-                 in, st);
+        e = lin_forward(s, tc, s->act[l], l, z, 5 * P, st);
         if (e != cudaSuccess) return e;
         if (l < s->nl - 1) {
             act_fwd_kernel<<<blocks_for(P * o), 256, 0, st>>>(z, s->act[l + 1], P, o);
@@ -607,6 +689,10 @@ cudaError_t forward_fp32(spo_surrogate *s, const float *pos, int64_t P, float *o
         }
     }
     return cudaSuccess;
+}
+
+cudaError_t forward_fp32(spo_surrogate *s, const float *pos, int64_t P, float *out, cudaStream_t st) {
+    return forward_train(s, pos, P, out, st, false);
 }
 
 spo_detail::SurrMlpView mlp_view(const spo_surrogate *s) {
@@ -655,15 +741,15 @@ cudaError_t channel_weights_for(spo_surrogate *s, const float *target, int64_t P
 // Forward, loss (into dacc[0]) and backward over P positions; the gradient
 // is added to s->grad.
 cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, int64_t P,
-                     const ChannelWeights &cw, cudaStream_t st) {
+                     const ChannelWeights &cw, cudaStream_t st, bool tc) {
     const int64_t N = s->spec.N;
-    const int M = (int)(5 * P);
+    const int64_t M = 5 * P;
     float *out = s->gbuf[0];   // network output [P][5][N] (gbuf holds max width >= N columns)
-    cudaError_t e = forward_fp32(s, pos, P, out, st);
+    cudaError_t e = forward_train(s, pos, P, out, st, tc);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dacc, 0, sizeof(double), st);
     if (e == cudaSuccess) {
-        loss_kernel<<<(unsigned)std::min<int64_t>(P * 5, 152 * 8), 256, 0, st>>>(out, target, P, N, cw, s->gbuf[1],
-                                                                                  s->dacc);
+        loss_kernel<<<dim3((unsigned)std::min<int64_t>(P, 152 * 4), 5), 256, 0, st>>>(out, target, P, N, cw,
+                                                                                       s->gbuf[1], s->dacc);
         e = cudaGetLastError();
     }
     // g = gbuf[gi] is d loss / d output of layer l; the two buffers alternate
@@ -677,15 +763,14 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
             e = cudaGetLastError();
             gi = 1 - gi;
         }
-        if (e == cudaSuccess)
-            e = gemm(2, false, gz, s->act[l], s->grad + s->w_off[l], nullptr, o, in, M, o, in, st);
+        if (e == cudaSuccess) e = lin_wgrad(s, tc, gz, s->act[l], l, M, st);
         if (e == cudaSuccess) {
             bias_grad_kernel<<<dim3((o + 127) / 128, (unsigned)std::min<int64_t>(P, 256)), 128, 0, st>>>(
                 gz, P, o, s->grad + s->b_off[l]);
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {   // d loss / d input of layer l
-            e = gemm(1, false, gz, s->param + s->w_off[l], s->gbuf[1 - gi], nullptr, M, in, o, o, in, st);
+            e = lin_dgrad(s, tc, gz, l, s->gbuf[1 - gi], M, st);
             gi = 1 - gi;
         }
     }
@@ -848,6 +933,8 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
     cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
     cudaFree(s->feat);
+    cudaFree(s->img[0]);
+    cudaFree(s->img[1]);
     delete s;
     return SPO_OK;
 }
@@ -931,10 +1018,11 @@ spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos,
 }
 
 spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *target, int64_t P,
-                              const float *channel_weights, float *loss, float *grid, float *const *W,
-                              float *const *b, void *stream) {
+                              const float *channel_weights, int precision, float *loss, float *grid,
+                              float *const *W, float *const *b, void *stream) {
     fail(SPO_OK, "");
     if (!s || !pos || !target || !grid || !W || !b) return fail(SPO_EINVAL, "NULL argument");
+    if (precision != 0 && precision != 1) return fail(SPO_EINVAL, "precision must be 0 or 1");
     if (P < 1 || P > (1 << 20)) return fail(SPO_EINVAL, "need 1 <= P <= 2^20");
     DeviceGuard guard(s->device);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -943,7 +1031,7 @@ spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *t
     ChannelWeights cw{};
     cudaError_t e = channel_weights_for(s, target, P, channel_weights, cw, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->grad, 0, sizeof(float) * s->nparam, st);
-    if (e == cudaSuccess) e = backward(s, pos, target, P, cw, st);
+    if (e == cudaSuccess) e = backward(s, pos, target, P, cw, st, precision == 1);
     double loss_h = 0.0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&loss_h, s->dacc, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grid, s->grad, sizeof(float) * s->grid_n, cudaMemcpyDeviceToHost, st);
@@ -989,7 +1077,7 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
             return es;
         }
         if (step == 0) e = channel_weights_for(s, s->target, P, channel_weights, cw, st);
-        if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st);
+        if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st, s->train_precision == 1);
         if (e == cudaSuccess) {
             ++s->adam_t;
             const float b1 = s->beta1, b2 = s->beta2;
@@ -1029,6 +1117,14 @@ spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta
     s->beta2 = beta2;
     s->eps = eps;
     s->grid_lr_mult = grid_lr_mult;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_set_train_precision(spo_surrogate *s, int precision) {
+    fail(SPO_OK, "");
+    if (!s) return fail(SPO_EINVAL, "surrogate is NULL");
+    if (precision != 0 && precision != 1) return fail(SPO_EINVAL, "precision must be 0 or 1");
+    s->train_precision = precision;
     return SPO_OK;
 }
 

@@ -67,4 +67,18 @@ cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const S
                                float *out, bool values_only, int num_sms, uint8_t *feat,
                                cudaStream_t stream);
 
+// BF16 tile images of GEMM operands (tiles of 128 rows x 64 K-columns in the
+// 128-byte swizzle layout, zero beyond the matrix) and the tensor-core GEMM
+// that reads them (spo_tc_gemm.cu).
+size_t bf16_image_bytes(int64_t rows, int64_t K);
+// src: FP32 [R][C] row major, leading dimension ld.  transpose = false: the
+// image of src (rows R, K = C); true: the image of src^T (rows C, K = R).
+cudaError_t to_bf16_image(const float *src, int64_t R, int64_t C, int64_t ld, bool transpose, uint8_t *img,
+                          cudaStream_t stream);
+// C[M][N] (row major, ld N) = A B^T from the images of A [M][K] and B [N][K];
+// accumulate: atomically added to C (K split across CTAs); otherwise stored,
+// with bias[n] added to the rows m % 5 == 0 when bias is not null.
+cudaError_t tc_gemm(const uint8_t *a_img, const uint8_t *b_img, int64_t M, int64_t N, int64_t K, float *C,
+                    const float *bias, bool accumulate, cudaStream_t stream);
+
 }  // namespace spo_detail

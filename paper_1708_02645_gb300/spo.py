@@ -63,8 +63,9 @@ SIGNATURES = [
     ("spo_surrogate_train", _INT, [_P, _P, _I64, _I64, ctypes.c_float, _P, ctypes.c_uint64, _P,
                                    ctypes.POINTER(ctypes.c_float)]),
     ("spo_surrogate_eval", _INT, [_P, _INT, _P, _I64, _P, _INT, _P]),
-    ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, ctypes.POINTER(ctypes.c_float), _P, _P, _P,
-                                  _P]),
+    ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, _INT, ctypes.POINTER(ctypes.c_float), _P, _P,
+                                  _P, _P]),
+    ("spo_surrogate_set_train_precision", _INT, [_P, _INT]),
     ("spo_surrogate_set_optimizer", _INT, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_float]),
     ("spo_surrogate_nparams", _INT, [_P, ctypes.POINTER(_I64)]),
@@ -557,9 +558,10 @@ class Surrogate:
                "spo_surrogate_train")
         return float(loss.value)
 
-    def grad(self, pos, target, channel_weights=None, stream=None):
+    def grad(self, pos, target, channel_weights=None, precision=0, stream=None):
         """Loss and FP32 gradients (grid, W list, b list) for device positions
-        [P, 3] and device targets [P, 5, N]; the parameters are unchanged."""
+        [P, 3] and device targets [P, 5, N]; the parameters are unchanged.
+        precision 1: the products as tensor-core training computes them."""
         torch = _torch()
         for t in (pos, target):
             if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
@@ -573,7 +575,7 @@ class Surrogate:
         loss = ctypes.c_float()
         _check(load().spo_surrogate_grad(self._h, ctypes.c_void_p(pos.data_ptr()),
                                          ctypes.c_void_p(target.data_ptr()), int(pos.shape[0]), cw,
-                                         ctypes.byref(loss), grid.ctypes.data, Wp, bp,
+                                         int(precision), ctypes.byref(loss), grid.ctypes.data, Wp, bp,
                                          _stream_handle(stream)), "spo_surrogate_grad")
         return float(loss.value), grid, W, b
 
@@ -595,6 +597,11 @@ class Surrogate:
         n = ctypes.c_size_t()
         _check(load().spo_surrogate_footprint(self._h, ctypes.byref(n)), "spo_surrogate_footprint")
         return int(n.value)
+
+    def set_train_precision(self, precision: int):
+        """1: training products on the tensor cores (BF16), 0: FP32."""
+        _check(load().spo_surrogate_set_train_precision(self._h, int(precision)),
+               "spo_surrogate_set_train_precision")
 
     def set_optimizer(self, beta1=0.9, beta2=0.99, eps=1e-15, grid_lr_mult=1.0):
         _check(load().spo_surrogate_set_optimizer(self._h, float(beta1), float(beta2), float(eps),

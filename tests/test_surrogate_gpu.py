@@ -97,6 +97,31 @@ def test_fused_tile_sizing_edges(spo_lib, P):
     assert max(err) < 4e-3, err
 
 
+@pytest.mark.parametrize("spec,P", [(RAGGED, 257), (FULL, 200)])
+def test_tensor_core_gradients_match_rounded_reference(spo_lib, spec, P):
+    """precision 1: the forward, weight-gradient and data-gradient products
+    on the tensor cores with BF16 operands against the reference that rounds
+    the same operands (tolerance 2e-3 of max |ref| per array: FP32
+    accumulation order, and an operand whose FP32 and FP64 values straddle a
+    bfloat16 rounding boundary now and then)."""
+    t = torch()
+    p = S.as_float32(S.init_params(spec, seed=34, grid_scale=0.3))
+    pos = inputs.uniform_positions(P, 35)
+    target = inputs.normal(36, P * 5 * spec.N).reshape(P, 5, spec.N).astype(np.float32)
+    wch = [1.0, 0.25, 0.25, 0.25, 0.01]
+    L, gg, gW, gb = S.grads(p, pos.astype(np.float64), target.astype(np.float64), wch,
+                            gemm_round=S.round_bf16)
+    with load(spo_lib, spec, p) as s:
+        loss, ggot, Wgot, bgot = s.grad(t.from_numpy(pos).cuda(), t.from_numpy(target).cuda(),
+                                        channel_weights=wch, precision=1)
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    assert abs(loss - L) < 1e-4 * abs(L)
+    for got, ref in [(ggot, gg)] + list(zip(Wgot, gW)) + list(zip(bgot, gb)):
+        err = np.abs(got - ref).max() / np.abs(ref).max()
+        assert err < 2e-3, err
+
+
 @pytest.mark.parametrize("given", [True, False])
 def test_gradients_match_reference(spo_lib, given):
     t = torch()

@@ -134,3 +134,22 @@ def test_quantised_forward_is_close_and_rounds_inputs():
         scale = np.abs(exact[:, c]).max()
         assert np.abs(q[:, c] - exact[:, c]).max() < 0.05 * scale
         assert np.abs(q[:, c] - exact[:, c]).max() > 0.0
+
+
+def test_gemm_rounding_reading():
+    """The tensor-core training reading (both operands of every product
+    rounded to bfloat16): with the identity as rounding it is the exact
+    backward bit for bit; with bfloat16 it stays within a few roundings."""
+    p = small_params(seed=6)
+    pos = inputs.uniform_positions(24, 10).astype(np.float64)
+    target = np.random.default_rng(3).normal(size=(24, 5, SMALL.N))
+    wch = [1.0, 0.3, 0.3, 0.3, 0.05]
+    exact = S.grads(p, pos, target, wch)
+    same = S.grads(p, pos, target, wch, gemm_round=lambda x: x)
+    assert exact[0] == same[0]
+    for a, b in zip([exact[1]] + exact[2] + exact[3], [same[1]] + same[2] + same[3]):
+        assert np.array_equal(a, b)
+    bf = S.grads(p, pos, target, wch, gemm_round=S.round_bf16)
+    assert abs(bf[0] - exact[0]) < 0.05 * abs(exact[0])
+    for a, b in zip(exact[2], bf[2]):
+        assert 0 < np.abs(a - b).max() < 0.1 * np.abs(a).max()
