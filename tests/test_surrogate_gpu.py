@@ -97,7 +97,12 @@ def test_fused_tile_sizing_edges(spo_lib, P):
     assert max(err) < 4e-3, err
 
 
-@pytest.mark.parametrize("spec,P", [(RAGGED, 257), (FULL, 200)])
+# widths that are not multiples of 8 (the GEMM's scalar epilogue) and odd
+# row counts
+ODD = S.SurrogateSpec(levels=3, log2_table=9, features=2, r_min=3, r_max=11, hidden=36, layers=2, N=20)
+
+
+@pytest.mark.parametrize("spec,P", [(RAGGED, 257), (FULL, 200), (ODD, 131)])
 def test_tensor_core_gradients_match_rounded_reference(spo_lib, spec, P):
     """precision 1: the forward, weight-gradient and data-gradient products
     on the tensor cores with BF16 operands against the reference that rounds
