@@ -11,30 +11,17 @@
 #include <new>
 
 #include "spo.h"
+#include "spo_host.h"
 #include "spo_internal.h"
 
 namespace {
 
+using spo_detail::cuda_fail;
+using spo_detail::DeviceGuard;
 using spo_detail::fail;
 
 thread_local char g_last_error[512] = "";
 
-// Restores the caller's current device when it goes out of scope.
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int device) {
-        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
-        if (prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev_ >= 0) cudaSetDevice(prev_);
-    }
-    bool ok() const { return ok_; }
-
-  private:
-    int prev_ = -1;
-    bool ok_ = true;
-};
 
 size_t dtype_size(spo_dtype t) {
     switch (t) {
@@ -48,9 +35,6 @@ size_t dtype_size(spo_dtype t) {
 
 bool valid_kind(spo_kind k) { return k == SPO_KIND_V || k == SPO_KIND_VGL || k == SPO_KIND_VGH; }
 
-spo_status cuda_fail(cudaError_t e, const char *what) {
-    return fail(SPO_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
-}
 
 // pointer must be device or managed memory on `device`
 spo_status check_device_pointer(const void *ptr, int device, const char *name) {

@@ -13,6 +13,7 @@
 #include "spo.h"
 #include "spo_batch.h"
 #include "spo_device.cuh"
+#include "spo_host.h"
 #include "spo_internal.h"
 
 struct spo_batch {
@@ -50,6 +51,8 @@ namespace {
 
 using spo_detail::BatchParams;
 using spo_detail::BatchSetDesc;
+using spo_detail::cuda_fail;
+using spo_detail::DeviceGuard;
 using spo_detail::fail;
 using spo_detail::kBrick;
 
@@ -118,9 +121,6 @@ void free_plan(spo_batch *b) {
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
 }
 
-spo_status cuda_fail(cudaError_t e, const char *what) {
-    return fail(SPO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
 BatchParams make_params(const spo_batch *b, spo_kind kind, int tile, int64_t Ptot) {
     BatchParams bp;
@@ -223,21 +223,6 @@ spo_status stage_items(spo_batch *b, const spo_work *items, int nitems, const in
     return e == cudaSuccess ? SPO_OK : cuda_fail(e, "item table upload");
 }
 
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int device) {
-        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
-        if (prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev_ >= 0) cudaSetDevice(prev_);
-    }
-    bool ok() const { return ok_; }
-
-  private:
-    int prev_ = -1;
-    bool ok_ = true;
-};
 
 }  // namespace
 

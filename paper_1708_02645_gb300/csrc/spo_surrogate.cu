@@ -23,12 +23,15 @@
 #include <vector>
 
 #include "spo.h"
+#include "spo_host.h"
 #include "spo_internal.h"
 #include "spo_surrogate.h"
 #include "spo_surrogate_enc.cuh"
 
 namespace {
 
+using spo_detail::cuda_fail;
+using spo_detail::DeviceGuard;
 using spo_detail::fail;
 using spo_detail::SurrLevels;
 using spo_dev::level_corners;
@@ -781,25 +784,7 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     return e;
 }
 
-class DeviceGuard {
-  public:
-    explicit DeviceGuard(int device) {
-        if (cudaGetDevice(&prev_) != cudaSuccess) prev_ = -1;
-        if (prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        if (prev_ >= 0) cudaSetDevice(prev_);
-    }
-    bool ok() const { return ok_; }
 
-  private:
-    int prev_ = -1;
-    bool ok_ = true;
-};
-
-spo_status cuda_fail(cudaError_t e, const char *what) {
-    return fail(SPO_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
 }  // namespace
 
