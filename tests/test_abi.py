@@ -86,3 +86,39 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(spo, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         spo.load()
+
+
+def test_newer_entry_points_reject_bad_arguments_before_cuda(lib):
+    """Surrogate, prefilter, batch and self-test calls check their
+    arguments on the host and return SPO_EINVAL (1) before any CUDA call."""
+    from paper_1708_02645_gb300 import spo
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(0x1000)
+    bad = spo._SurrogateSpec(0, 19, 2, 16, 512, 128, 3, 0, 384)         # no levels
+    good = spo._SurrogateSpec(16, 19, 2, 16, 512, 128, 3, 0, 384)
+    assert lib.spo_surrogate_create(ctypes.byref(bad), 0, ctypes.byref(h)) == 1
+    assert lib.spo_surrogate_create(ctypes.byref(good), 0, None) == 1
+    wide = spo._SurrogateSpec(16, 19, 2, 16, 512, 128, 9, 0, 384)        # too many layers
+    assert lib.spo_surrogate_create(ctypes.byref(wide), 0, ctypes.byref(h)) == 1
+    assert h.value is None
+    loss = ctypes.c_float()
+    assert lib.spo_surrogate_eval(None, 1, fake, 1, fake, 1, None) == 1
+    assert lib.spo_surrogate_train(None, None, 1, 1, 1e-3, None, 0, None, ctypes.byref(loss)) == 1
+    assert lib.spo_surrogate_grad(None, fake, fake, 1, None, 0, ctypes.byref(loss), fake, fake, fake,
+                                  None) == 1
+    b = ctypes.c_size_t()
+    assert lib.spo_surrogate_footprint(None, ctypes.byref(b)) == 1
+    assert lib.spo_surrogate_set_optimizer(None, 0.9, 0.99, 1e-15, 1.0) == 1
+    assert lib.spo_surrogate_set_train_precision(None, 1) == 1
+    n = ctypes.c_int64()
+    assert lib.spo_surrogate_nparams(None, ctypes.byref(n)) == 1
+    assert lib.spo_surrogate_destroy(None) == 0
+    grid = spo._Grid(8, 8, 8)
+    assert lib.spo_prefilter(None, 4, fake, 0, None) == 1
+    assert lib.spo_prefilter(ctypes.byref(grid), 0, fake, 0, None) == 1
+    assert lib.spo_prefilter(ctypes.byref(grid), 4, fake, 3, None) == 1       # FP16 data
+    t = ctypes.c_int()
+    assert lib.spo_selftest_wait(2_000_000_000, None, ctypes.byref(t)) == 1
+    assert lib.spo_selftest_wait(1000, None, None) == 1
+    assert lib.spo_eval_batch(None, 0, None, 0, 2, None) == 1
+    assert lib.spo_batch_create(None, 0, 1, 1, ctypes.byref(h)) == 1
