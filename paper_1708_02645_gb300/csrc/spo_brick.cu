@@ -53,8 +53,14 @@ struct BrickShape {
 // RATIO (KIND = V only): each position's values are also multiplied by its
 // row of A^-1 and reduced over the position's lanes; one partial dot product
 // per (tile, position) goes to ra.partials.  out may then be nullptr.
-template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false>
-__global__ void __launch_bounds__(BrickShape<TILE>::threads, BrickShape<TILE>::ctas_per_sm)
+//
+// PAIR: one CTA per (z-adjacent pair of bricks, tile); the pair's block is
+// one 7 x 7 x 11-node TMA box (69 KB for 32 FP32 orbitals, 3 CTAs per SM)
+// and its positions are the two bricks' contiguous ranges of the sorted
+// order, so each CTA evaluates twice as many positions per staged node and
+// per start-up.  The arithmetic per position is unchanged (same bits).
+template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false, bool PAIR = false>
+__global__ void __launch_bounds__(BrickShape<TILE>::threads, PAIR ? 3 : BrickShape<TILE>::ctas_per_sm)
 spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
                  int nby, int nbz, int ntiles, int64_t N, const int *__restrict__ offsets,
                  const float4 *__restrict__ sorted, float *__restrict__ out, int eager,
@@ -66,14 +72,20 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     constexpr int kVec = V;                   // orbitals per thread
     constexpr int TPP = TILE / kVec;          // threads per position
     constexpr int PPR = kThreads / TPP;       // positions per round
-    constexpr uint32_t kBytes = kBlockRows * TILE * sizeof(T);
+    constexpr int kBZ = PAIR ? 2 * kBrick + 3 : kBlockEdge;   // block nodes along z
+    constexpr uint32_t kBytes = kBlockEdge * kBlockEdge * kBZ * TILE * sizeof(T);
     extern __shared__ __align__(128) unsigned char smem[];
     T *block = reinterpret_cast<T *>(smem);   // [7][7][7][TILE]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBytes);
 
     const int brick = blockIdx.x / ntiles;
     const int tile = blockIdx.x - brick * ntiles;
-    const int bz = brick % nbz, by = (brick / nbz) % nby, bx = brick / (nbz * nby);
+    // brick (bx, by, bz) is bin (bx nby + by) nbz + bz of the sorted order
+    const int nbzu = PAIR ? (nbz + 1) / 2 : nbz;
+    const int bzu = brick % nbzu, by = (brick / nbzu) % nby, bx = brick / (nbzu * nby);
+    const int bz = PAIR ? 2 * bzu : bzu;
+    const int b0 = (bx * nby + by) * nbz + bz;
+    const int b1 = b0 + ((PAIR && bz + 1 < nbz) ? 2 : 1);
     const uint32_t bar_s = smem_addr(bar);
 
     // With `eager` (bricks hold several positions on average) the copy is
@@ -81,8 +93,8 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     // otherwise empty bricks are skipped before any copy.
     int begin = 0, end = 0;
     if (!eager) {
-        begin = __ldg(offsets + brick);
-        end = __ldg(offsets + brick + 1);
+        begin = __ldg(offsets + b0);
+        end = __ldg(offsets + b1);
         if (begin == end) return;
     }
     if (threadIdx.x == 0) {
@@ -93,8 +105,8 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
         tma_load_4d(smem_addr(block), &map, bar_s, tile * TILE, bz * kBrick, by * kBrick, bx * kBrick);
     }
     if (eager) {
-        begin = __ldg(offsets + brick);
-        end = __ldg(offsets + brick + 1);
+        begin = __ldg(offsets + b0);
+        end = __ldg(offsets + b1);
     }
     __syncthreads();   // the barrier's initialisation is visible to every thread
     if (begin == end) {   // (eager only) nothing to do, but the copy must land first
@@ -127,13 +139,13 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
         // memory index in range even if it had not
         const int lx = min(max(X.cell - bx * kBrick, 0), kBrick - 1);
         const int ly = min(max(Y.cell - by * kBrick, 0), kBrick - 1);
-        const int lz = min(max(Z.cell - bz * kBrick, 0), kBrick - 1);
-        const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
+        const int lz = min(max(Z.cell - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
+        const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + q * kVec;
         float acc[NC][kVec];
         window_reduce<KIND, kVec, true>(X, gx, Y, Z,
                             [&](int a, int b, int g, float *v) {
                                 load_coefs<T, kVec, false>(
-                                    base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
+                                    base + ((a * kBlockEdge + b) * kBZ + g) * TILE, v);
                             },
                             acc);
         if constexpr (RATIO) {
@@ -363,18 +375,33 @@ spo_brick_pipe_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, Grid
 template <typename T, int KIND, int TILE, int V>
 cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P, float *out,
                          cudaStream_t stream) {
-    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
     const int nbins = s->nbx * s->nby * s->nbz;
     const int ntiles = (int)((s->N + TILE - 1) / TILE);
+    const bool vec_out = (s->N % V == 0) && ((reinterpret_cast<uintptr_t>(out) % (4 * V)) == 0);
+    const int eager = P >= 4 * (int64_t)nbins;   // about 4+ positions per brick
+    if constexpr (TILE == 32) {
+      if (s->has_pair_map) {   // 32-orbital tiles on z-adjacent brick pairs
+        constexpr size_t kSmemP = (size_t)kBlockEdge * kBlockEdge * (2 * kBrick + 3) * TILE * sizeof(T) + 16;
+        const int64_t blocks = (int64_t)s->nbx * s->nby * ((s->nbz + 1) / 2) * ntiles;
+        if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+        auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true, false, true>
+                              : spo_brick_kernel<T, KIND, TILE, V, false, false, true>;
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemP);
+        if (e != cudaSuccess) return e;
+        kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmemP, stream>>>(
+            s->block_map[2], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles,
+            s->N, w.offsets, w.sorted, out, eager, spo_detail::RatioArgs{});
+        return cudaGetLastError();
+      }
+    }
+    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
     const int64_t blocks = (int64_t)nbins * ntiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool vec_out = (s->N % V == 0) && ((reinterpret_cast<uintptr_t>(out) % (4 * V)) == 0);
     auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true>
                           : spo_brick_kernel<T, KIND, TILE, V, false>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
-    const int eager = P >= 4 * (int64_t)nbins;   // about 4+ positions per brick
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
         w.offsets, w.sorted, out, eager, spo_detail::RatioArgs{});
@@ -535,6 +562,15 @@ spo_status make_block_map(spo_set *s) {
         if (r != CUDA_SUCCESS) return fail(SPO_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     }
     s->has_block_map = true;
+    // brick pairs along z: box (32, 11, 7, 7), for grids of at least two bricks in z
+    s->has_pair_map = false;
+    if (s->nbz >= 2 && s->zp >= 2 * kBrick + 3) {
+        const cuuint32_t box[4] = {32, 2 * kBrick + 3, kBlockEdge, kBlockEdge};
+        const CUresult r = enc(&s->block_map[2], dt, 4, s->table, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        s->has_pair_map = r == CUDA_SUCCESS;
+    }
     return SPO_OK;
 }
 

@@ -58,8 +58,10 @@ struct spo_set {
     // strategy chosen by spo_autotune for each kind, for batches near tuned_P
     int tuned_algo[3] = {0, 0, 0};
     int64_t tuned_P[3] = {0, 0, 0};
-    CUtensorMap block_map[2];   // 4-D TMA maps of the table, boxes (32 | 64, 7, 7, 7)
+    CUtensorMap block_map[3];   // 4-D TMA maps of the table, boxes (32 | 64, 7, 7, 7) and
+                                // (32, 11, 7, 7) for z-adjacent brick pairs
     bool has_block_map = false; // Np >= 32: the brick kernel can serve this set
+    bool has_pair_map = false;  // block_map[2] exists (nz >= 8): 32-orbital tiles run on brick pairs
 
     // scratch of the binned path, one per stream (guarded by mu)
     std::mutex mu;

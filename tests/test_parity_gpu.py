@@ -107,7 +107,8 @@ def test_nio64_full_batch_sampled(spo_lib, oracle_lib, nio64, storage):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("grid,N", [((4, 4, 4), 1), ((5, 9, 7), 13), ((4, 6, 5), 7),
                                     ((8, 8, 8), 33), ((7, 4, 11), 4), ((6, 6, 6), 1024),
-                                    ((9, 10, 11), 100), ((4, 5, 6), 65), ((13, 6, 9), 64)])
+                                    ((9, 10, 11), 100), ((4, 5, 6), 65), ((13, 6, 9), 64),
+                                    ((12, 10, 20), 40)])
 @pytest.mark.parametrize("kind", ["v", "vgl", "vgh"])
 def test_ragged_shapes(spo_lib, oracle_lib, grid, N, kind):
     """Grids that are not multiples of the brick edge (partial bricks at the
