@@ -73,7 +73,8 @@ def measured_hbm_peak():
 
 # the files the brick kernel is compiled from (its recorded DRAM traffic goes
 # stale when any of them changes)
-BRICK_SOURCES = ("spo_brick.cu", "spo_device.cuh", "spo_tma.cuh", "spo_internal.h", "spo_batch.h")
+BRICK_SOURCES = ("spo_brick.cu", "spo_brick.cuh", "spo_brick_f32.cu", "spo_brick_bf16.cu", "spo_brick_f16.cu",
+                 "spo_device.cuh", "spo_tma.cuh", "spo_internal.h", "spo_batch.h")
 
 
 def kernel_source_digest() -> str:

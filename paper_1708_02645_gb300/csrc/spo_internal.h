@@ -62,6 +62,7 @@ struct spo_set {
                                 // (32, 11, 7, 7) for z-adjacent brick pairs
     bool has_block_map = false; // Np >= 32: the brick kernel can serve this set
     bool has_pair_map = false;  // block_map[2] exists (nz >= 8): 32-orbital tiles run on brick pairs
+    unsigned int *status = nullptr;   // device status word (bit 0: a bounded wait gave up)
 
     // scratch of the binned path, one per stream (guarded by mu)
     std::mutex mu;
@@ -127,6 +128,15 @@ struct RatioArgs {
     float *partials;        // [ntiles][P]
     int64_t P;
 };
+
+// The brick kernels of one storage type T (float, __nv_bfloat16, __half),
+// instantiated in spo_brick_f32.cu, spo_brick_bf16.cu and spo_brick_f16.cu.
+template <typename T>
+cudaError_t brick_eval_typed(spo_kind kind, const spo_set *set, const Workspace &w, int64_t P, float *out,
+                             cudaStream_t stream);
+template <typename T>
+cudaError_t brick_ratio_typed(const spo_set *set, const Workspace &w, int64_t P, float *out,
+                              const RatioArgs &ra, cudaStream_t stream);
 
 // Brick kernel for V with the ratio epilogue: per (tile, position) partial
 // dot products into r.partials; values to out unless out is nullptr.

@@ -758,7 +758,7 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     // g = gbuf[gi] is d loss / d output of layer l; the two buffers alternate
     int gi = 1;
     for (int l = s->nl - 1; l >= 0 && e == cudaSuccess; --l) {
-        const int in = s->widths[l], o = s->widths[l + 1];
+        const int o = s->widths[l + 1];
         float *gz = s->gbuf[gi];
         if (l < s->nl - 1) {   // through the softplus of layer l
             gz = s->gbuf[1 - gi];
