@@ -56,6 +56,49 @@ struct BrickShape {
     static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
 };
 
+// Weight slot of one position (kSlotF4 float4 in shared memory): x-node
+// weights (w, w', w'', 0) for nodes 0..3, then y's w[4], w'[4], w''[4], then
+// z's, then the cells (x, y, z, -) as ints.  Lanes 0, 1 and 2 of a
+// position's group each reduce one axis and form its four nodes' weights
+// (reduce_axis and node_weights, the functions every kernel uses, so the
+// bits are those of the gather kernel); the whole group then reads them.
+// Forming the 36 weights once per position instead of once per lane takes
+// about 100 scalar FP32 operations per lane and position off the FMA pipe.
+constexpr int kSlotF4 = 11;
+
+// bytes of the weight slots of a CTA: one slot per position of a round
+template <int TILE, int V>
+constexpr size_t kSlotBytes = (size_t)(BrickShape<TILE>::threads / (TILE / V)) * kSlotF4 * 16;
+
+__device__ __forceinline__ void unpack4(const float4 &r, float (&v)[4]) {
+    v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
+}
+
+__device__ __forceinline__ void stage_axis_weights(int q, const float4 &r, const GridAxis &gx,
+                                                   const GridAxis &gy, const GridAxis &gz,
+                                                   float4 *slot) {
+    const int a = q < 3 ? q : 0;   // lanes 3.. of the group repeat the x axis and store nothing
+    const GridAxis g = a == 0 ? gx : (a == 1 ? gy : gz);
+    const float u = a == 0 ? r.x : (a == 1 ? r.y : r.z);
+    int cell;
+    float t, w[4], d[4], dd[4];
+    reduce_axis(u, g, cell, t);
+    node_weights<0>(t, g, w[0], d[0], dd[0]);
+    node_weights<1>(t, g, w[1], d[1], dd[1]);
+    node_weights<2>(t, g, w[2], d[2], dd[2]);
+    node_weights<3>(t, g, w[3], d[3], dd[3]);
+    if (q == 0) {
+#pragma unroll
+        for (int n = 0; n < 4; ++n) slot[n] = make_float4(w[n], d[n], dd[n], 0.0f);
+    } else if (q < 3) {
+        float4 *s = slot + 4 + 3 * (q - 1);
+        s[0] = make_float4(w[0], w[1], w[2], w[3]);
+        s[1] = make_float4(d[0], d[1], d[2], d[3]);
+        s[2] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+    }
+    if (q < 3) reinterpret_cast<int *>(slot + 10)[q] = cell;
+}
+
 // RATIO (KIND = V only): each position's values are also multiplied by its
 // row of A^-1 and reduced over the position's lanes; one partial dot product
 // per (tile, position) goes to ra.partials.  out may then be nullptr.
@@ -83,6 +126,7 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     extern __shared__ __align__(1024) unsigned char smem[];
     T *block = reinterpret_cast<T *>(smem);   // [7][7][7][TILE]
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBytes);
+    float4 *wslots = reinterpret_cast<float4 *>(smem + kBytes + 16);   // [PPR][kSlotF4]
 
     const int brick = blockIdx.x / ntiles;
     const int tile = blockIdx.x - brick * ntiles;
@@ -122,56 +166,69 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
 
     const int q = threadIdx.x % TPP;
     const int64_t o0 = (int64_t)tile * TILE + q * kVec;   // first orbital of this thread
+    // positions are taken in rounds of PPR; the trip count of the loop is
+    // uniform over each warp (groups past the end sit the round out), so the
+    // warp can share the weight slots
+    const int wg0 = (int)(threadIdx.x >> 5) * (32 / TPP);   // first position group of this warp
+    float4 *slot = wslots + (threadIdx.x / TPP) * kSlotF4;
     int i = begin + threadIdx.x / TPP;
     // each round's position record (x, y, z, index) was loaded one round early
     float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     bool ready = false;
-    for (; i < end; i += PPR) {
+    for (int ib = begin + wg0; ib < end; ib += PPR, i += PPR) {
         const float4 nxt = i + PPR < end ? __ldg(sorted + i + PPR) : cur;
         const int p = __float_as_int(cur.w);
-        XAxis X;
-        Axis Y, Z;
-        make_xaxis(cur.x, gx, X);
-        make_axis(cur.y, gy, Y);
-        make_axis(cur.z, gz, Z);
-        if (!ready) {   // the first position's weights were computed while the copy flew
-            if (!mbar_wait_bounded(bar_s, 0)) {
-                atomicOr(status, 1u);
+        __syncwarp();   // the previous round's reads of the slots are done
+        stage_axis_weights(q, cur, gx, gy, gz, slot);
+        __syncwarp();
+        if (!ready) {   // the first round's weights were formed while the copy flew
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_s, 0))) {
+                if ((threadIdx.x & 31) == 0) atomicOr(status, 1u);
                 return;
             }
             ready = true;
         }
-        // the binning put the cell in this brick; the clamp keeps the shared
-        // memory index in range even if it had not
-        const int lx = min(max(X.cell - bx * kBrick, 0), kBrick - 1);
-        const int ly = min(max(Y.cell - by * kBrick, 0), kBrick - 1);
-        const int lz = min(max(Z.cell - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
-        const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + q * kVec;
-        float acc[NC][kVec];
-        window_reduce<KIND, kVec, true>(X, gx, Y, Z,
-                            [&](int a, int b, int g, float *v) {
-                                load_coefs<T, kVec, false>(
-                                    base + ((a * kBlockEdge + b) * kBZ + g) * TILE, v);
-                            },
-                            acc);
-        if constexpr (RATIO) {
-            int r = ra.row_of ? __ldg(ra.row_of + p) : p;
-            r = (int)min(max((int64_t)r, (int64_t)0), ra.nrows - 1);
-            const float *arow = ra.rows + (int64_t)r * ra.ld + o0;
-            float dot = 0.0f;
+        if (i < end) {
+            Axis Y, Z;
+            const int4 cells = *reinterpret_cast<const int4 *>(slot + 10);
+            unpack4(slot[4], Y.w);
+            unpack4(slot[5], Y.d);
+            unpack4(slot[6], Y.dd);
+            unpack4(slot[7], Z.w);
+            unpack4(slot[8], Z.d);
+            unpack4(slot[9], Z.dd);
+            // the binning put the cell in this brick; the clamp keeps the
+            // shared memory index in range even if it had not
+            const int lx = min(max(cells.x - bx * kBrick, 0), kBrick - 1);
+            const int ly = min(max(cells.y - by * kBrick, 0), kBrick - 1);
+            const int lz = min(max(cells.z - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
+            const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + q * kVec;
+            float acc[NC][kVec];
+            window_reduce_staged<KIND, kVec, true>(slot, Y, Z,
+                                [&](int a, int b, int g, float *v) {
+                                    load_coefs<T, kVec, false>(
+                                        base + ((a * kBlockEdge + b) * kBZ + g) * TILE, v);
+                                },
+                                acc);
+            if constexpr (RATIO) {
+                int r = ra.row_of ? __ldg(ra.row_of + p) : p;
+                r = (int)min(max((int64_t)r, (int64_t)0), ra.nrows - 1);
+                const float *arow = ra.rows + (int64_t)r * ra.ld + o0;
+                float dot = 0.0f;
 #pragma unroll
-            for (int k = 0; k < kVec; ++k)
-                if (o0 + k < N) dot = fmaf(acc[0][k], __ldg(arow + k), dot);
-            // the TPP lanes of this position form an aligned group of the warp
-            const unsigned lane = threadIdx.x & 31u;
-            const unsigned gmask = TPP >= 32 ? 0xffffffffu
-                                             : (((1u << TPP) - 1u) << (lane & ~(unsigned)(TPP - 1)));
+                for (int k = 0; k < kVec; ++k)
+                    if (o0 + k < N) dot = fmaf(acc[0][k], __ldg(arow + k), dot);
+                // the TPP lanes of this position form an aligned group of the warp
+                const unsigned lane = threadIdx.x & 31u;
+                const unsigned gmask = TPP >= 32 ? 0xffffffffu
+                                                 : (((1u << TPP) - 1u) << (lane & ~(unsigned)(TPP - 1)));
 #pragma unroll
-            for (int off = TPP / 2; off > 0; off >>= 1) dot += __shfl_xor_sync(gmask, dot, off);
-            if (q == 0) ra.partials[(int64_t)tile * ra.P + p] = dot;
+                for (int off = TPP / 2; off > 0; off >>= 1) dot += __shfl_xor_sync(gmask, dot, off);
+                if (q == 0) ra.partials[(int64_t)tile * ra.P + p] = dot;
+            }
+            if (o0 < N && (!RATIO || out != nullptr))
+                store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
         }
-        if (o0 < N && (!RATIO || out != nullptr))
-            store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
         cur = nxt;
     }
     if (!ready && threadIdx.x == 0) {
@@ -387,7 +444,8 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
     const int eager = P >= 4 * (int64_t)nbins;   // about 4+ positions per brick
     if constexpr (TILE == 32) {
       if (s->has_pair_map) {   // 32-orbital tiles on z-adjacent brick pairs
-        constexpr size_t kSmemP = (size_t)kBlockEdge * kBlockEdge * (2 * kBrick + 3) * TILE * sizeof(T) + 16;
+        constexpr size_t kSmemP = (size_t)kBlockEdge * kBlockEdge * (2 * kBrick + 3) * TILE * sizeof(T) + 16 +
+                                 kSlotBytes<TILE, V>;
         const int64_t blocks = (int64_t)s->nbx * s->nby * ((s->nbz + 1) / 2) * ntiles;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
         auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true, false, true>
@@ -396,11 +454,12 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
         if (e != cudaSuccess) return e;
         kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmemP, stream>>>(
             s->block_map[2], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles,
-            s->N, w.offsets, w.sorted, out, eager, spo_detail::RatioArgs{}, s->status);
+            s->N, w.offsets, w.sorted, out, eager,
+            spo_detail::RatioArgs{}, s->status);
         return cudaGetLastError();
       }
     }
-    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
+    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16 + kSlotBytes<TILE, V>;
     const int64_t blocks = (int64_t)nbins * ntiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true>
@@ -410,14 +469,15 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
     const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, out, eager, spo_detail::RatioArgs{}, s->status);
+        w.offsets, w.sorted, out, eager,
+        spo_detail::RatioArgs{}, s->status);
     return cudaGetLastError();
 }
 
 template <typename T, int TILE, int V>
 cudaError_t brick_ratio_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P,
                                float *out, const spo_detail::RatioArgs &ra, cudaStream_t stream) {
-    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
+    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16 + kSlotBytes<TILE, V>;
     const int nbins = s->nbx * s->nby * s->nbz;
     const int ntiles = (int)((s->N + TILE - 1) / TILE);
     const int64_t blocks = (int64_t)nbins * ntiles;
@@ -431,7 +491,8 @@ cudaError_t brick_ratio_launch(const spo_set *s, const spo_detail::Workspace &w,
     const int eager = P >= 4 * (int64_t)nbins;
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, out, eager, ra, s->status);
+        w.offsets, w.sorted, out, eager,
+        ra, s->status);
     return cudaGetLastError();
 }
 

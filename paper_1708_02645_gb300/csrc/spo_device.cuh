@@ -437,6 +437,26 @@ __device__ __forceinline__ void window_reduce(const XAxis &X, const GridAxis &gx
     window_x_node<KIND, V, 3>(xw, xd, xdd, Y, Z, load, acc);
 }
 
+// window_reduce with the x-node weights taken from xs[A] = (w, w', w'', -)
+// (formed elsewhere by node_weights<A>, so the sums carry the same bits).
+// With FENCE each node's weights are read after the previous node's
+// arithmetic.
+template <int KIND, int V, bool FENCE, typename Load>
+__device__ __forceinline__ void window_reduce_staged(const float4 *xs, const Axis &Y, const Axis &Z,
+                                                     Load load, float (&acc)[Rows<KIND>::value][V]) {
+    float4 x = xs[0];
+    window_x_node<KIND, V, 0>(x.x, x.y, x.z, Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    x = xs[1];
+    window_x_node<KIND, V, 1>(x.x, x.y, x.z, Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    x = xs[2];
+    window_x_node<KIND, V, 2>(x.x, x.y, x.z, Y, Z, load, acc);
+    if constexpr (FENCE) asm volatile("" ::: "memory");
+    x = xs[3];
+    window_x_node<KIND, V, 3>(x.x, x.y, x.z, Y, Z, load, acc);
+}
+
 // Streaming store of the NC x V results of one thread; o points at this
 // thread's first orbital in component 0 of one position, N is the row
 // stride, `left` orbitals remain in the row from that first orbital.  With
