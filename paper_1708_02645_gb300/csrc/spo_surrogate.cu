@@ -532,8 +532,19 @@ struct spo_surrogate {
     size_t feat_cap = 0;
 
     int train_precision = 1;            // 1: training GEMMs on the tensor cores (BF16), 0: FP32
-    uint8_t *img[2] = {nullptr, nullptr};   // GEMM operand images for the tensor-core training
-    size_t img_cap[2] = {0, 0};
+    // BF16 operand images of the tensor-core training, carved from one arena:
+    // ia, ib (A-side scratch of one product), and per layer xt (X^T, kept
+    // from the forward pass to the weight gradient), wd (W) and wt (W^T)
+    uint8_t *img = nullptr;
+    size_t img_cap = 0;
+    uint8_t *ia = nullptr, *ib = nullptr;
+    uint8_t *xt[kMaxLayers] = {}, *wd[kMaxLayers] = {}, *wt[kMaxLayers] = {};
+    int64_t img_M = 0;                  // rows the carve-up was made for
+
+    // samples and spline values of a run of training steps, drawn and
+    // evaluated together (grown)
+    float *tpos = nullptr, *ttarget = nullptr;
+    int64_t tcap = 0;
 };
 
 namespace {
@@ -546,6 +557,29 @@ void free_scratch(spo_surrogate *s) {
     for (auto &a : s->gbuf) { cudaFree(a); a = nullptr; }
     s->pos = s->target = nullptr;
     s->cap_P = 0;
+    cudaFree(s->tpos);
+    cudaFree(s->ttarget);
+    s->tpos = s->ttarget = nullptr;
+    s->tcap = 0;
+}
+
+// Room for the samples and spline values of n positions (a run of steps).
+spo_status grow_teacher(spo_surrogate *s, int64_t n) {
+    if (s->tcap >= n) return SPO_OK;
+    cudaFree(s->tpos);
+    cudaFree(s->ttarget);
+    s->tpos = s->ttarget = nullptr;
+    s->tcap = 0;
+    cudaError_t e = cudaMalloc(&s->tpos, sizeof(float) * 3 * (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->ttarget, sizeof(float) * 5 * (size_t)n * s->spec.N);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->tpos);
+        s->tpos = nullptr;
+        return fail(SPO_ENOMEM, "training samples for %lld positions failed", (long long)n);
+    }
+    s->tcap = n;
+    return SPO_OK;
 }
 
 spo_status grow_scratch(spo_surrogate *s, int64_t P) {
@@ -614,61 +648,78 @@ cudaError_t gemm(int mode, bool bf16, const float *A, const void *B, float *C, c
     return cudaGetLastError();
 }
 
-// Operand images for the tensor-core form of the three products of layer
-// l over M = 5 P rows: forward (X [M][in], W [o][in]), weight gradient
-// (gz^T, X^T: K = M) and data gradient (gz [M][o], W^T).
+// Operand images for the tensor-core form of the three products of each
+// layer over M = 5 P rows: forward (X [M][in] and W [o][in]), weight
+// gradient (gz^T and X^T, K = M) and data gradient (gz [M][o] and W^T).
 cudaError_t ensure_images(spo_surrogate *s, int64_t M) {
-    size_t need[2] = {0, 0};
+    if (s->img_M == M && s->img) return cudaSuccess;
+    auto al = [](size_t b) { return (b + 1023) & ~size_t(1023); };
+    size_t a = 0, b = 0, per[kMaxLayers][3] = {};
+    size_t total = 0;
     for (int l = 0; l < s->nl; ++l) {
         const int64_t in = s->widths[l], o = s->widths[l + 1];
-        need[0] = std::max({need[0], spo_detail::bf16_image_bytes(M, in), spo_detail::bf16_image_bytes(o, M),
-                            spo_detail::bf16_image_bytes(M, o)});
-        need[1] = std::max({need[1], spo_detail::bf16_image_bytes(o, in), spo_detail::bf16_image_bytes(in, M),
-                            spo_detail::bf16_image_bytes(in, o)});
+        a = std::max({a, al(spo_detail::bf16_image_bytes(M, in)), al(spo_detail::bf16_image_bytes(o, M))});
+        b = std::max(b, al(spo_detail::bf16_image_bytes(M, o)));
+        per[l][0] = al(spo_detail::bf16_image_bytes(in, M));
+        per[l][1] = al(spo_detail::bf16_image_bytes(o, in));
+        per[l][2] = al(spo_detail::bf16_image_bytes(in, o));
+        total += per[l][0] + per[l][1] + per[l][2];
     }
-    for (int k = 0; k < 2; ++k) {
-        if (s->img_cap[k] >= need[k]) continue;
-        cudaFree(s->img[k]);
-        s->img[k] = nullptr;
-        s->img_cap[k] = 0;
-        const cudaError_t e = cudaMalloc(&s->img[k], need[k]);
+    total += a + b;
+    if (s->img_cap < total) {
+        cudaFree(s->img);
+        s->img = nullptr;
+        s->img_cap = 0;
+        s->img_M = 0;
+        const cudaError_t e = cudaMalloc(&s->img, total);
         if (e != cudaSuccess) return e;
-        s->img_cap[k] = need[k];
+        s->img_cap = total;
     }
+    uint8_t *p = s->img;
+    s->ia = p;
+    p += a;
+    s->ib = p;
+    p += b;
+    for (int l = 0; l < s->nl; ++l) {
+        s->xt[l] = p;
+        p += per[l][0];
+        s->wd[l] = p;
+        p += per[l][1];
+        s->wt[l] = p;
+        p += per[l][2];
+    }
+    s->img_M = M;
     return cudaSuccess;
 }
 
-// Z [M][o] = X [M][in] W_l^T, plus b_l on the value rows
+// Z [M][o] = X [M][in] W_l^T, plus b_l on the value rows.  Tensor-core form:
+// X's two images in one pass (X^T kept for the weight gradient), W's images
+// made at the start of the pass.
 cudaError_t lin_forward(spo_surrogate *s, bool tc, const float *X, int l, float *Z, int64_t M, cudaStream_t st) {
     const int in = s->widths[l], o = s->widths[l + 1];
     const float *W = s->param + s->w_off[l], *b = s->param + s->b_off[l];
     if (!tc) return gemm(0, false, X, W, Z, b, (int)M, o, in, in, in, st);
-    cudaError_t e = spo_detail::to_bf16_image(X, M, in, in, false, s->img[0], st);
-    if (e == cudaSuccess) e = spo_detail::to_bf16_image(W, o, in, in, false, s->img[1], st);
-    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], M, o, in, Z, b, false, st);
+    cudaError_t e = spo_detail::to_bf16_images(X, M, in, in, s->ia, s->xt[l], st);
+    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->ia, s->wd[l], M, o, in, Z, b, false, st);
     return e;
 }
 
-// dW_l [o][in] += gz [M][o]^T X [M][in]
-cudaError_t lin_wgrad(spo_surrogate *s, bool tc, const float *gz, const float *X, int l, int64_t M,
-                      cudaStream_t st) {
+// dW_l [o][in] += gz [M][o]^T X [M][in] and G [M][in] = gz [M][o] W_l [o][in]
+// (G may be null: no data gradient).  Tensor-core form: gz's two images in
+// one pass, X^T and W^T from the forward pass.
+cudaError_t lin_backward(spo_surrogate *s, bool tc, const float *gz, const float *X, int l, float *G, int64_t M,
+                         cudaStream_t st) {
     const int in = s->widths[l], o = s->widths[l + 1];
     float *dW = s->grad + s->w_off[l];
-    if (!tc) return gemm(2, false, gz, X, dW, nullptr, o, in, (int)M, o, in, st);
-    cudaError_t e = spo_detail::to_bf16_image(gz, M, o, o, true, s->img[0], st);
-    if (e == cudaSuccess) e = spo_detail::to_bf16_image(X, M, in, in, true, s->img[1], st);
-    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], o, in, M, dW, nullptr, true, st);
-    return e;
-}
-
-// G [M][in] = gz [M][o] W_l [o][in]
-cudaError_t lin_dgrad(spo_surrogate *s, bool tc, const float *gz, int l, float *G, int64_t M, cudaStream_t st) {
-    const int in = s->widths[l], o = s->widths[l + 1];
     const float *W = s->param + s->w_off[l];
-    if (!tc) return gemm(1, false, gz, W, G, nullptr, (int)M, in, o, o, in, st);
-    cudaError_t e = spo_detail::to_bf16_image(gz, M, o, o, false, s->img[0], st);
-    if (e == cudaSuccess) e = spo_detail::to_bf16_image(W, o, in, in, true, s->img[1], st);
-    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->img[0], s->img[1], M, in, o, G, nullptr, false, st);
+    if (!tc) {
+        cudaError_t e = gemm(2, false, gz, X, dW, nullptr, o, in, (int)M, o, in, st);
+        if (e == cudaSuccess && G) e = gemm(1, false, gz, W, G, nullptr, (int)M, in, o, o, in, st);
+        return e;
+    }
+    cudaError_t e = spo_detail::to_bf16_images(gz, M, o, o, s->ib, s->ia, st);
+    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->ia, s->xt[l], o, in, M, dW, nullptr, true, st);
+    if (e == cudaSuccess && G) e = spo_detail::tc_gemm(s->ib, s->wt[l], M, in, o, G, nullptr, false, st);
     return e;
 }
 
@@ -681,6 +732,11 @@ cudaError_t forward_train(spo_surrogate *s, const float *pos, int64_t P, float *
                                                                              s->act[0]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (tc && (e = ensure_images(s, 5 * P)) != cudaSuccess) return e;
+    for (int l = 0; l < s->nl && tc; ++l) {   // W and W^T of every layer
+        const int in = s->widths[l], o = s->widths[l + 1];
+        e = spo_detail::to_bf16_images(s->param + s->w_off[l], o, in, in, s->wd[l], s->wt[l], st);
+        if (e != cudaSuccess) return e;
+    }
     for (int l = 0; l < s->nl; ++l) {
         const int o = s->widths[l + 1];
         float *z = (l == s->nl - 1 && out) ? out : s->pre[l];
@@ -766,14 +822,13 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
             e = cudaGetLastError();
             gi = 1 - gi;
         }
-        if (e == cudaSuccess) e = lin_wgrad(s, tc, gz, s->act[l], l, M, st);
         if (e == cudaSuccess) {
             bias_grad_kernel<<<dim3((o + 127) / 128, (unsigned)std::min<int64_t>(P, 256)), 128, 0, st>>>(
                 gz, P, o, s->grad + s->b_off[l]);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) {   // d loss / d input of layer l
-            e = lin_dgrad(s, tc, gz, l, s->gbuf[1 - gi], M, st);
+        if (e == cudaSuccess) {   // weight gradient and d loss / d input of layer l
+            e = lin_backward(s, tc, gz, s->act[l], l, s->gbuf[1 - gi], M, st);
             gi = 1 - gi;
         }
     }
@@ -918,8 +973,7 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     cudaFree(s->param); cudaFree(s->grad); cudaFree(s->m1); cudaFree(s->m2);
     cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
     cudaFree(s->feat);
-    cudaFree(s->img[0]);
-    cudaFree(s->img[1]);
+    cudaFree(s->img);
     delete s;
     return SPO_OK;
 }
@@ -1048,21 +1102,39 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
     spo_status rs = grow_scratch(s, batch);
     if (rs != SPO_OK) return rs;
     const int64_t P = batch;
+    // The samples of `run` consecutive steps are drawn at once (the same
+    // counter-based stream as one step at a time) and the spline's VGL at
+    // all of them is one evaluation: about 32 positions per brick of the
+    // teacher's binning instead of the few of one batch, at most 1 GiB of
+    // spline values.
+    const int64_t nbins = (int64_t)teacher->nbx * teacher->nby * teacher->nbz;
+    const int64_t per_step = (int64_t)5 * P * s->spec.N * (int64_t)sizeof(float);
+    int64_t run = std::max<int64_t>(1, (32 * nbins + P - 1) / P);
+    run = std::min<int64_t>(run, std::max<int64_t>(1, (INT64_C(1) << 30) / per_step));
+    run = std::max<int64_t>(1, std::min<int64_t>(run, steps));
+    rs = grow_teacher(s, run * P);
+    if (rs != SPO_OK) return rs;
     ChannelWeights cw{};
     double loss_h = 0.0;
     cudaError_t e = cudaSuccess;
     for (int64_t step = 0; step < steps && e == cudaSuccess; ++step) {
-        sample_kernel<<<blocks_for(3 * P), 256, 0, st>>>(s->pos, 3 * P, seed,
-                                                           (unsigned long long)step * 3 * P);
-        const spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->pos, P, s->target, st,
-                                                     SPO_ALGO_AUTO);
-        if (es != SPO_OK) {   // keep the inference copies in step with the parameters taken so far
-            refresh_inference(s, st);
-            cudaStreamSynchronize(st);
-            return es;
+        const int64_t k = step % run;
+        if (k == 0) {
+            const int64_t n = std::min<int64_t>(run, steps - step) * P;
+            sample_kernel<<<blocks_for(3 * n), 256, 0, st>>>(s->tpos, 3 * n, seed,
+                                                               (unsigned long long)step * 3 * P);
+            const spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->tpos, n, s->ttarget, st,
+                                                         SPO_ALGO_AUTO);
+            if (es != SPO_OK) {   // keep the inference copies in step with the parameters taken so far
+                refresh_inference(s, st);
+                cudaStreamSynchronize(st);
+                return es;
+            }
         }
-        if (step == 0) e = channel_weights_for(s, s->target, P, channel_weights, cw, st);
-        if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st, s->train_precision == 1);
+        const float *pos = s->tpos + 3 * k * P;
+        const float *target = s->ttarget + 5 * k * P * s->spec.N;
+        if (step == 0) e = channel_weights_for(s, target, P, channel_weights, cw, st);
+        if (e == cudaSuccess) e = backward(s, pos, target, P, cw, st, s->train_precision == 1);
         if (e == cudaSuccess) {
             ++s->adam_t;
             const float b1 = s->beta1, b2 = s->beta2;

@@ -75,6 +75,10 @@ size_t bf16_image_bytes(int64_t rows, int64_t K);
 // image of src (rows R, K = C); true: the image of src^T (rows C, K = R).
 cudaError_t to_bf16_image(const float *src, int64_t R, int64_t C, int64_t ld, bool transpose, uint8_t *img,
                           cudaStream_t stream);
+// Both images of the R x C matrix in one pass: img_direct as
+// to_bf16_image(..., false, ...) and img_transposed as (..., true, ...).
+cudaError_t to_bf16_images(const float *src, int64_t R, int64_t C, int64_t ld, uint8_t *img_direct,
+                           uint8_t *img_transposed, cudaStream_t stream);
 // C[M][N] (row major, ld N) = A B^T from the images of A [M][K] and B [N][K];
 // accumulate: atomically added to C (K split across CTAs); otherwise stored,
 // with bias[n] added to the rows m % 5 == 0 when bias is not null.

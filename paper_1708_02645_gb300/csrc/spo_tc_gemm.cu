@@ -81,6 +81,56 @@ __global__ void to_image_kernel(const float *__restrict__ src, int64_t R, int64_
     }
 }
 
+// Both images of an FP32 row-major R x C matrix in one pass: img_d with
+// image rows = source rows (K = C) and img_t with image rows = source
+// columns (K = R).  A CTA stages one 64 x 64 block through shared memory
+// (blocks cover the source padded to multiples of 128 in both directions,
+// so the zero padding of both images is written too) and writes its 16-byte
+// chunks of each image; the block index is linear (nbc blocks per row of
+// blocks).
+__global__ void __launch_bounds__(256) to_image2_kernel(const float *__restrict__ src, int64_t R, int64_t C,
+                                                        int64_t ld, int64_t nbc, int64_t rows_pad_d,
+                                                        int64_t kc_n_d, uint8_t *__restrict__ img_d,
+                                                        int64_t rows_pad_t, int64_t kc_n_t,
+                                                        uint8_t *__restrict__ img_t) {
+    __shared__ float tile[64][65];
+    const int64_t br = (int64_t)blockIdx.x / nbc;
+    const int64_t r0 = br * 64, c0 = ((int64_t)blockIdx.x - br * nbc) * 64;
+    const int tcol = threadIdx.x & 63, trow = threadIdx.x >> 6;
+#pragma unroll 4
+    for (int k = 0; k < 16; ++k) {
+        const int r = trow + 4 * k;
+        const int64_t gr = r0 + r, gc = c0 + tcol;
+        tile[r][tcol] = (gr < R && gc < C) ? __ldg(src + gr * ld + gc) : 0.0f;
+    }
+    __syncthreads();
+    const int64_t KBd = kc_n_d / 8, KBt = kc_n_t / 8;
+    // direct: chunk (r, q) = image row r0 + r, K columns c0 + 8q .. c0 + 8q + 7
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int r = e >> 3, q = e & 7;
+        const int64_t row = r0 + r, kc = c0 / 8 + q;
+        if (row < rows_pad_d && kc < kc_n_d) {
+            const float *v = &tile[r][8 * q];
+            uint8_t *t = img_d + (size_t)((row / kRowsT) * KBd + kc / 8) * kTileBytes;
+            *reinterpret_cast<uint4 *>(t + sw128_offset((int)(row % kRowsT), q * 8)) =
+                make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+        }
+    }
+    // transposed: chunk (cc, q) = image row c0 + cc, K rows r0 + 8q .. r0 + 8q + 7
+    for (int e = threadIdx.x; e < 512; e += 256) {
+        const int cc = e & 63, q = e >> 6;
+        const int64_t row = c0 + cc, kc = r0 / 8 + q;
+        if (row < rows_pad_t && kc < kc_n_t) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = tile[8 * q + j][cc];
+            uint8_t *t = img_t + (size_t)((row / kRowsT) * KBt + kc / 8) * kTileBytes;
+            *reinterpret_cast<uint4 *>(t + sw128_offset((int)(row % kRowsT), q * 8)) =
+                make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+        }
+    }
+}
+
 struct GemmArgs {
     const uint8_t *a, *b;
     int64_t M, N;
@@ -229,6 +279,19 @@ cudaError_t to_bf16_image(const float *src, int64_t R, int64_t C, int64_t ld, bo
     if (total == 0) return cudaSuccess;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     to_image_kernel<<<blocks, 256, 0, stream>>>(src, R, C, ld, transpose ? 1 : 0, rows_pad, kc_n, img);
+    return cudaGetLastError();
+}
+
+cudaError_t to_bf16_images(const float *src, int64_t R, int64_t C, int64_t ld, uint8_t *img_direct,
+                           uint8_t *img_transposed, cudaStream_t stream) {
+    if (R <= 0 || C <= 0) return cudaSuccess;
+    const int64_t rp_d = (R + kRowsT - 1) / kRowsT * kRowsT, kc_d = (C + kColsT - 1) / kColsT * 8;
+    const int64_t rp_t = (C + kRowsT - 1) / kRowsT * kRowsT, kc_t = (R + kColsT - 1) / kColsT * 8;
+    const int64_t nbr = rp_d / 64, nbc = rp_t / 64;   // 64 x 64 blocks over the padded source
+    const int64_t blocks = nbr * nbc;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    to_image2_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, R, C, ld, nbc, rp_d, kc_d, img_direct, rp_t,
+                                                           kc_t, img_transposed);
     return cudaGetLastError();
 }
 
