@@ -127,6 +127,25 @@ def test_ragged_reduced_precision(spo_lib, oracle_lib, storage, N):
     check_case(spo_lib, c, pos, "vgh", storage, what=f"ragged {storage}", algos=["auto"] + ALGOS)
 
 
+@pytest.mark.parametrize("kind", ["v", "vgh"])
+def test_f16_special_values(spo_lib, oracle_lib, kind):
+    """FP16 tables holding zeros of both signs, subnormals, the smallest and
+    largest normals and values that round into the subnormal range, mixed
+    with ordinary ones: the kernels widen every stored half exactly (normal
+    halves by integer operations, the rest by the library conversion)."""
+    rng = np.random.default_rng(23)
+    special = np.array([0.0, -0.0, 2.0 ** -24, -(2.0 ** -24), 3 * 2.0 ** -24, 2.0 ** -15,
+                        2.0 ** -14, -(2.0 ** -14), 2.0 ** -14 - 2.0 ** -24, 65504.0, -65504.0,
+                        1e-5, -3e-6, 0.75, -1.5])
+    grid, N = (8, 9, 10), 40
+    c = rng.choice(special, size=grid + (N,))
+    ordinary = rng.uniform(-2.0, 2.0, size=c.shape)
+    c = np.where(rng.uniform(size=c.shape) < 0.5, c, ordinary)
+    pos = np.concatenate([inputs.uniform_positions(3001, 21), inputs.wide_positions(500, 22)])
+    check_case(spo_lib, c, pos, kind, "f16", what=f"f16 special values {kind}",
+               algos=["auto"] + ALGOS)
+
+
 def test_degenerate_position_clouds(spo_lib, oracle_lib):
     """All positions in one cell (one brick holds every position), all at one
     point, and a single position: every strategy."""
