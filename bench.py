@@ -513,6 +513,10 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+VARIANTS = ("all", "storage", "ratio", "autotune", "crowd", "surrogate", "surrogate_specified", "prefilter",
+            "nio32")
+
+
 def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
     """Reduced-precision storage on the same positions (throughput, table
     bytes, and the GPU-side difference from the FP32-storage outputs), and
@@ -521,7 +525,12 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
     from paper_1708_02645_gb300 import spo
     res = {}
     steps = max(5, min(args.steps, 50))
-    if storage == "f32":
+    chosen = set(args.variants.split(","))
+
+    def want(name):
+        return "all" in chosen or name in chosen
+
+    if storage == "f32" and want("storage"):
         ref = out32.clone()
         for st in ("bf16", "f16"):
             with spo.OrbitalSet(coefs32, storage=st) as sv:
@@ -536,7 +545,35 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
                            "table_bytes": sv.footprint(),
                            "max_rel_diff_vs_f32_storage": max_rel_diff(o, ref, kind)}
         res["f32_table_bytes"] = s32.footprint()
-    # fused value + determinant ratio (one row of A^-1 per position)
+    if want("ratio"):
+        res["ratio_fused_v"] = measure_ratio(cfg, s32, pos, steps)
+    if want("autotune"):
+        res["autotune"] = s32.autotune(kind, pos.shape[0])
+        configure(s32, args)   # back to the command line's tuning
+    if want("crowd"):
+        res["crowd"] = measure_crowd(args, kind, steps)
+    if cfg.N == 384 and (want("surrogate") or "surrogate_specified" in chosen):
+        res["surrogate"] = measure_surrogate(cfg, s32, pos, steps, coarse_run=want("surrogate"))
+    if want("prefilter"):
+        res["prefilter"] = measure_prefilter(cfg)
+    if want("nio32"):
+        n32 = inputs.NIO32
+        c = n32.make_coefs(np.float32)
+        p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
+        with spo.OrbitalSet(c, storage="f32") as sv:
+            configure(sv, args)
+            for kd in ("v", "vgl", "vgh"):
+                o = torch.empty(sv.out_shape(n32.P, kd), dtype=torch.float32, device=pos.device)
+                a = resolve_algo(args.algo, sv, n32.P)
+                step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
+                res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
+                                           "ms_per_step": round(step_ms, 5), "algo": a}
+    return res
+
+
+def measure_ratio(cfg, s32, pos, steps):
+    """Fused value + determinant ratio: one row of A^-1 per position."""
+    import torch
     P = pos.shape[0]
     rows = (2.0 * torch.rand((P, cfg.N), device=pos.device, dtype=torch.float32,
                              generator=torch.Generator(device=pos.device).manual_seed(7)) - 1.0)
@@ -551,28 +588,10 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
     e1.record()
     torch.cuda.synchronize()
     r_ms = e0.elapsed_time(e1) / steps
-    res["ratio_fused_v"] = {"value": P * cfg.N / (r_ms * 1e-3), "unit": "evals/s",
-                            "ratios_per_s": P / (r_ms * 1e-3), "ms_per_step": round(r_ms, 5),
-                            "what": "spo_eval_ratio: V of all orbitals dotted with an A^-1 row "
-                                    "per position, values not stored"}
-    res["autotune"] = s32.autotune(kind, pos.shape[0])
-    configure(s32, args)   # back to the command line's tuning
-    res["crowd"] = measure_crowd(args, kind, steps)
-    if cfg.N == 384:
-        res["surrogate"] = measure_surrogate(cfg, s32, pos, steps)
-    res["prefilter"] = measure_prefilter(cfg)
-    n32 = inputs.NIO32
-    c = n32.make_coefs(np.float32)
-    p32 = torch.from_numpy(n32.make_positions()).to(pos.device)
-    with spo.OrbitalSet(c, storage="f32") as sv:
-        configure(sv, args)
-        for kd in ("v", "vgl", "vgh"):
-            o = torch.empty(sv.out_shape(n32.P, kd), dtype=torch.float32, device=pos.device)
-            a = resolve_algo(args.algo, sv, n32.P)
-            step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
-            res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
-                                       "ms_per_step": round(step_ms, 5), "algo": a}
-    return res
+    return {"value": P * cfg.N / (r_ms * 1e-3), "unit": "evals/s",
+            "ratios_per_s": P / (r_ms * 1e-3), "ms_per_step": round(r_ms, 5),
+            "what": "spo_eval_ratio: V of all orbitals dotted with an A^-1 row per position, "
+                    "values not stored"}
 
 
 def measure_prefilter(cfg):
@@ -671,7 +690,7 @@ def surrogate_run(spec, teacher, pos, steps, phases, batch=16384, grid_lr_mult=1
     return res
 
 
-def measure_surrogate(cfg, teacher, pos, steps):
+def measure_surrogate(cfg, teacher, pos, steps, coarse_run=True):
     """Learned surrogates of the 384-orbital set: the specified one (16
     levels x 2^19 x 2 FP16 hashed grid at resolutions 16..512, 32-128-128-
     128-384 BF16 perceptron, 2^22 training samples) and the same network with
@@ -685,6 +704,8 @@ def measure_surrogate(cfg, teacher, pos, steps):
     spec = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=16, r_max=512, hidden=128,
                            layers=3, N=cfg.N)
     res["specified"] = surrogate_run(spec, teacher, pos, steps, [(1e-3, 256, 1.0)])
+    if not coarse_run:
+        return res
     coarse = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=4, r_max=64, hidden=128,
                              layers=3, N=cfg.N)
     res["coarse_levels"] = surrogate_run(coarse, teacher, pos, steps, [(1e-3, 4096, 0.85)])
@@ -805,9 +826,16 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the BF16/FP16 and NiO-32-shaped sub-results")
+    ap.add_argument("--variants", default="all",
+                    help="comma list of the sub-results to measure: storage, ratio, autotune, crowd, "
+                         "surrogate (both networks), surrogate_specified (the specified network "
+                         "only), prefilter, nio32 (default all)")
     ap.add_argument("--positions", type=int, default=0,
                     help="evaluate this many positions instead of the workload's (profiling)")
     args = ap.parse_args(argv)
+    unknown = set(args.variants.split(",")) - set(VARIANTS)
+    if unknown:
+        ap.error(f"unknown --variants {sorted(unknown)}; choose from {VARIANTS}")
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
