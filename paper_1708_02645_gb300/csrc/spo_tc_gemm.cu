@@ -32,10 +32,11 @@ using namespace spo_dev;
 
 constexpr int kRowsT = 128, kColsT = 64;
 constexpr uint32_t kTileBytes = kRowsT * kColsT * 2;   // 16 KB
-constexpr int kStages = 3;
+constexpr int kMaxStages = 3;
 constexpr uint32_t kStageBytes = 2 * kTileBytes;       // A and B tiles
-constexpr uint32_t kOffBars = kStages * kStageBytes;   // full[3], empty[3], done, tmem slot
-constexpr uint32_t kSmem = kOffBars + 64 + 1024;
+// shared memory of a CTA with `stages` stages: the stages, then full[3],
+// empty[3], done and the tensor-memory slot (64 B), plus 1 KB of alignment
+constexpr uint32_t smem_bytes(int stages) { return (uint32_t)stages * kStageBytes + 64 + 1024; }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -140,6 +141,7 @@ struct GemmArgs {
     const float *bias; // added to rows i % 5 == 0 (stored form only)
     int accumulate;    // 1: atomically add into C
     int vec;           // N % 8 == 0 and C 32-byte aligned: 256-bit stores / 128-bit atomics
+    int stages;        // shared-memory stages, min(3, kb_per): short K leaves room for more CTAs per SM
     unsigned int *status;
 };
 
@@ -147,7 +149,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t s0 = smem_addr(sm);
-    const uint32_t full = s0 + kOffBars, empty = full + 8 * kStages, done = empty + 8 * kStages;
+    const int kStages = g.stages;
+    const uint32_t full = s0 + (uint32_t)kStages * kStageBytes, empty = full + 8 * kMaxStages,
+                   done = empty + 8 * kMaxStages;
     const uint32_t slot = done + 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool leader = threadIdx.x == 0;
@@ -319,10 +323,12 @@ cudaError_t tc_gemm(const uint8_t *a_img, const uint8_t *b_img, int64_t M, int64
     }
     g.kb_per = (g.KB + splits - 1) / splits;
     splits = std::max(1, (g.KB + g.kb_per - 1) / g.kb_per);
-    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    g.stages = std::min(kMaxStages, std::max(1, g.kb_per));
+    e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(kMaxStages));
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)mts, (unsigned)nts, (unsigned)splits);
-    tc_gemm_kernel<<<grid, 128, kSmem, stream>>>(g);
+    tc_gemm_kernel<<<grid, 128, smem_bytes(g.stages), stream>>>(g);
     return cudaGetLastError();
 }
 
