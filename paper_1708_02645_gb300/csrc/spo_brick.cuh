@@ -56,48 +56,10 @@ struct BrickShape {
     static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
 };
 
-// Weight slot of one position (kSlotF4 float4 in shared memory): x-node
-// weights (w, w', w'', 0) for nodes 0..3, then y's w[4], w'[4], w''[4], then
-// z's, then the cells (x, y, z, -) as ints.  Lanes 0, 1 and 2 of a
-// position's group each reduce one axis and form its four nodes' weights
-// (reduce_axis and node_weights, the functions every kernel uses, so the
-// bits are those of the gather kernel); the whole group then reads them.
-// Forming the 36 weights once per position instead of once per lane takes
-// about 100 scalar FP32 operations per lane and position off the FMA pipe.
-constexpr int kSlotF4 = 11;
-
 // bytes of the weight slots of a CTA: one slot per position of a round
 template <int TILE, int V>
 constexpr size_t kSlotBytes = (size_t)(BrickShape<TILE>::threads / (TILE / V)) * kSlotF4 * 16;
 
-__device__ __forceinline__ void unpack4(const float4 &r, float (&v)[4]) {
-    v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
-}
-
-__device__ __forceinline__ void stage_axis_weights(int q, const float4 &r, const GridAxis &gx,
-                                                   const GridAxis &gy, const GridAxis &gz,
-                                                   float4 *slot) {
-    const int a = q < 3 ? q : 0;   // lanes 3.. of the group repeat the x axis and store nothing
-    const GridAxis g = a == 0 ? gx : (a == 1 ? gy : gz);
-    const float u = a == 0 ? r.x : (a == 1 ? r.y : r.z);
-    int cell;
-    float t, w[4], d[4], dd[4];
-    reduce_axis(u, g, cell, t);
-    node_weights<0>(t, g, w[0], d[0], dd[0]);
-    node_weights<1>(t, g, w[1], d[1], dd[1]);
-    node_weights<2>(t, g, w[2], d[2], dd[2]);
-    node_weights<3>(t, g, w[3], d[3], dd[3]);
-    if (q == 0) {
-#pragma unroll
-        for (int n = 0; n < 4; ++n) slot[n] = make_float4(w[n], d[n], dd[n], 0.0f);
-    } else if (q < 3) {
-        float4 *s = slot + 4 + 3 * (q - 1);
-        s[0] = make_float4(w[0], w[1], w[2], w[3]);
-        s[1] = make_float4(d[0], d[1], d[2], d[3]);
-        s[2] = make_float4(dd[0], dd[1], dd[2], dd[3]);
-    }
-    if (q < 3) reinterpret_cast<int *>(slot + 10)[q] = cell;
-}
 
 // RATIO (KIND = V only): each position's values are also multiplied by its
 // row of A^-1 and reduced over the position's lanes; one partial dot product

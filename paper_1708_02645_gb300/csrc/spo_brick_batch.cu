@@ -42,9 +42,10 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
     constexpr int TPP = TILE / kVec;
     constexpr int PPR = kThreads / TPP;
     constexpr uint32_t kBytes = kBlockRows * TILE * sizeof(T);
-    extern __shared__ __align__(128) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     T *block = reinterpret_cast<T *>(smem);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBytes);
+    float4 *wslots = reinterpret_cast<float4 *>(smem + kBytes + 16);   // [PPR][kSlotF4]
 
     const int unit = blockIdx.x;
     int s = 0;
@@ -83,48 +84,67 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
     const int q = threadIdx.x % TPP;
     const int64_t N = d.N;
     const int64_t o0 = (int64_t)tile * TILE + q * kVec;
+    // rounds of PPR positions, the trip count uniform over each warp (the
+    // weight slots are shared within it), as in the single-set kernel
+    const int wg0 = (int)(threadIdx.x >> 5) * (32 / TPP);
+    float4 *slot = wslots + (threadIdx.x / TPP) * kSlotF4;
     int i = begin + threadIdx.x / TPP;
     float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
     float *ocur = i < end ? dst[i] : nullptr;
     bool ready = false;
-    for (; i < end; i += PPR) {
+    for (int ib = begin + wg0; ib < end; ib += PPR, i += PPR) {
         const bool more = i + PPR < end;
         const float4 nxt = more ? __ldg(sorted + i + PPR) : cur;
         float *onxt = more ? dst[i + PPR] : ocur;
-        XAxis X;
-        Axis Y, Z;
-        make_xaxis(cur.x, d.gx, X);
-        make_axis(cur.y, d.gy, Y);
-        make_axis(cur.z, d.gz, Z);
+        __syncwarp();   // the previous round's reads of the slots are done
+        stage_axis_weights(q, cur, d.gx, d.gy, d.gz, slot);
+        __syncwarp();
         if (!ready) {
-            if (!mbar_wait_bounded(bar_s, 0)) {
-                atomicOr(status, 1u);
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_s, 0))) {
+                if ((threadIdx.x & 31) == 0) atomicOr(status, 1u);
                 return;
             }
             ready = true;
         }
-        const int lx = min(max(X.cell - bx * kBrick, 0), kBrick - 1);
-        const int ly = min(max(Y.cell - by * kBrick, 0), kBrick - 1);
-        const int lz = min(max(Z.cell - bz * kBrick, 0), kBrick - 1);
-        const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
-        float acc[NC][kVec];
-        window_reduce<KIND, kVec, true>(X, d.gx, Y, Z,
-                            [&](int a, int b, int g, float *v) {
-                                load_coefs<T, kVec, false>(
-                                    base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
-                            },
-                            acc);
-        if (o0 < N) store_rows<NC, kVec, VEC_OUT>(ocur + o0, N, N - o0, acc);
+        if (i < end) {
+            Axis Y, Z;
+            const int4 cells = *reinterpret_cast<const int4 *>(slot + 10);
+            unpack4(slot[4], Y.w);
+            unpack4(slot[5], Y.d);
+            unpack4(slot[6], Y.dd);
+            unpack4(slot[7], Z.w);
+            unpack4(slot[8], Z.d);
+            unpack4(slot[9], Z.dd);
+            const int lx = min(max(cells.x - bx * kBrick, 0), kBrick - 1);
+            const int ly = min(max(cells.y - by * kBrick, 0), kBrick - 1);
+            const int lz = min(max(cells.z - bz * kBrick, 0), kBrick - 1);
+            const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
+            float acc[NC][kVec];
+            window_reduce_staged<KIND, kVec, true>(slot, Y, Z,
+                                [&](int a, int b, int g, float *v) {
+                                    load_coefs<T, kVec, false>(
+                                        base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
+                                },
+                                acc);
+            if (o0 < N) store_rows<NC, kVec, VEC_OUT>(ocur + o0, N, N - o0, acc);
+        }
         cur = nxt;
         ocur = onxt;
     }
     if (!ready && threadIdx.x == 0 && !mbar_wait_bounded(bar_s, 0)) atomicOr(status, 1u);
 }
 
+// dynamic shared memory: the 7x7x7-node block, the barrier, one weight slot
+// per position of a round
+template <typename T, int TILE>
+constexpr size_t batch_smem() {
+    return (size_t)kBlockRows * TILE * sizeof(T) + 16 + (size_t)(Shape<TILE>::threads / (TILE / kVec)) * kSlotF4 * 16;
+}
+
 template <typename T, int KIND, int TILE>
 cudaError_t launch_typed(const BatchParams &bp, const int *offsets, const float4 *sorted,
                          float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
-    constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16;
+    constexpr size_t kSmem = batch_smem<T, TILE>();
     auto kernel = vec_out ? spo_brick_batch_kernel<T, KIND, TILE, true>
                           : spo_brick_batch_kernel<T, KIND, TILE, false>;
     if (bp.total_units <= 0) return cudaSuccess;
@@ -158,8 +178,8 @@ cudaError_t launch_kind(spo_kind kind, int tile, const BatchParams &bp, const in
 template <typename T, int KIND>
 cudaError_t prepare_kind() {
     cudaError_t e = cudaSuccess;
-    const int s32 = (int)((size_t)kBlockRows * 32 * sizeof(T) + 16);
-    const int s64 = (int)((size_t)kBlockRows * 64 * sizeof(T) + 16);
+    const int s32 = (int)batch_smem<T, 32>();
+    const int s64 = (int)batch_smem<T, 64>();
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, true>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, false>,
