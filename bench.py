@@ -340,6 +340,25 @@ def fp32_peak_tflops(num_sms: int):
         f"{num_sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
 
 
+def smem_peak_gbs(num_sms: int):
+    """Shared-memory bandwidth: SMs x 32 banks x 4 bytes per clock x the
+    maximum SM clock (MEASURED_PEAKS.json)."""
+    mhz, src = 2070.0, "nominal max SM clock"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        pass
+    return num_sms * 128 * mhz * 1e6 / 1e9, f"{num_sms} SMs x 32 banks x 4 B x {mhz:.0f} MHz ({src})"
+
+
+def brick_smem_bytes(P: int, N: int, storage: str, tile: int) -> int:
+    """Shared-memory bytes the brick kernel's window sums read per launch:
+    64 staged coefficients per (position, orbital of every tile, the last
+    one padded to the tile)."""
+    return P * (-(-N // tile) * tile) * 64 * STORAGE_BYTES[storage]
+
+
 def configure(s, args):
     s.set_param("brick_vec", args.brick_vec)
     s.set_param("brick_tile", args.brick_tile)
@@ -468,6 +487,16 @@ def run_ours(args):
                 "compulsory_achieved": round(comp / (kernel_ms * 1e-3) / 1e9, 1),
                 "compulsory_frac": round(comp / (kernel_ms * 1e-3) / 1e9 / hbm_peak, 4)},
     }
+    if algo == "brick" and args.brick_schedule == 0:
+        tile = args.brick_tile if s.info()["Np"] >= 64 else 32
+        sb = brick_smem_bytes(P, cfg.N, storage, tile)
+        sp, ssrc = smem_peak_gbs(props.multi_processor_count)
+        roofline["smem"] = {"achieved": round(sb / (kernel_ms * 1e-3) / 1e9, 1), "peak": round(sp, 1),
+                            "unit": "GB/s", "frac": round(sb / (kernel_ms * 1e-3) / 1e9 / sp, 4),
+                            "peak_source": ssrc, "bytes_per_launch": sb,
+                            "note": "coefficient reads of the window sums from the staged blocks "
+                                    "(64 per evaluation); the bound of the V kernel, where each "
+                                    "read feeds one FMA"}
     assert spo.device_status() == 0, "a bounded device-side wait gave up"
 
     # end to end through the C ABI with host buffers (pinned), copies timed

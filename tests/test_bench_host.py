@@ -34,6 +34,20 @@ def test_traffic_record_is_dropped_when_kernel_changes(tmp_path, monkeypatch):
     assert bench.recorded_traffic("w", "f32", "vgh", "brick/t32/v4/s0") is None
 
 
+def test_brick_smem_bytes_count_padded_tiles():
+    # 64 staged coefficients per (position, orbital), the last tile padded
+    assert bench.brick_smem_bytes(1, 32, "f32", 32) == 32 * 64 * 4
+    assert bench.brick_smem_bytes(1, 33, "f32", 32) == 64 * 64 * 4
+    assert bench.brick_smem_bytes(2, 40, "bf16", 64) == 2 * 64 * 64 * 2
+    assert bench.brick_smem_bytes(98304, 384, "f32", 32) == 98304 * 384 * 256
+
+
+def test_smem_peak_is_derived_from_bank_count_and_clock():
+    gbs, src = bench.smem_peak_gbs(152)
+    assert abs(gbs - 152 * 128 * 2070e6 / 1e9) < 1e-6 or "MEASURED" in src
+    assert "banks" in src
+
+
 def test_fp32_peak_is_derived_from_unit_counts_and_clock():
     tf, src = bench.fp32_peak_tflops(152)
     assert abs(tf - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-6 or "MEASURED" in src
