@@ -27,6 +27,7 @@
 #include "spo_internal.h"
 #include "spo_surrogate.h"
 #include "spo_surrogate_enc.cuh"
+#include "spo_umma.cuh"
 
 namespace {
 
@@ -301,21 +302,42 @@ __device__ __forceinline__ void softplus_d(float z, float &sp, float &d1, float 
     d3 = d2 * (1.0f - 2.0f * sg);
 }
 
+// h = the five channels of softplus(z) for one unit: value, gradient, Laplacian
+__device__ __forceinline__ void act_fwd_one(const float *zp, int64_t W, float (&h)[5]) {
+    float sp, d1, d2, d3;
+    softplus_d(zp[0], sp, d1, d2, d3);
+    const float gx = zp[W], gy = zp[2 * W], gz = zp[3 * W], lz = zp[4 * W];
+    h[0] = sp;
+    h[1] = d1 * gx;
+    h[2] = d1 * gy;
+    h[3] = d1 * gz;
+    h[4] = d2 * (gx * gx + gy * gy + gz * gz) + d1 * lz;
+}
+
+// o = d loss / d z for one unit, from z and g = d loss / d h
+__device__ __forceinline__ void act_bwd_one(const float *zp, const float *gp, int64_t W, float (&o)[5]) {
+    float sp, d1, d2, d3;
+    softplus_d(zp[0], sp, d1, d2, d3);
+    const float zx = zp[W], zy = zp[2 * W], zz = zp[3 * W], zl = zp[4 * W];
+    const float g0 = gp[0], gxv = gp[W], gyv = gp[2 * W], gzv = gp[3 * W], gl = gp[4 * W];
+    const float g2 = zx * zx + zy * zy + zz * zz;
+    o[0] = g0 * d1 + (gxv * zx + gyv * zy + gzv * zz) * d2 + gl * (d3 * g2 + d2 * zl);
+    o[1] = gxv * d1 + 2.0f * gl * d2 * zx;
+    o[2] = gyv * d1 + 2.0f * gl * d2 * zy;
+    o[3] = gzv * d1 + 2.0f * gl * d2 * zz;
+    o[4] = gl * d1;
+}
+
 __global__ void act_fwd_kernel(const float *__restrict__ z, float *__restrict__ h, int64_t P, int W) {
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * W;
          it += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = it / W;
         const int j = (int)(it - p * W);
-        const float *zp = z + p * 5 * W + j;
-        float sp, d1, d2, d3;
-        softplus_d(zp[0], sp, d1, d2, d3);
-        const float gx = zp[W], gy = zp[2 * W], gz = zp[3 * W], lz = zp[4 * W];
+        float o[5];
+        act_fwd_one(z + p * 5 * W + j, W, o);
         float *hp = h + p * 5 * W + j;
-        hp[0] = sp;
-        hp[W] = d1 * gx;
-        hp[2 * W] = d1 * gy;
-        hp[3 * W] = d1 * gz;
-        hp[4 * W] = d2 * (gx * gx + gy * gy + gz * gz) + d1 * lz;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) hp[c * W] = o[c];
     }
 }
 
@@ -325,20 +347,103 @@ __global__ void act_bwd_kernel(const float *__restrict__ z, const float *__restr
          it += (int64_t)gridDim.x * blockDim.x) {
         const int64_t p = it / W;
         const int j = (int)(it - p * W);
-        const float *zp = z + p * 5 * W + j;
-        const float *gp = g + p * 5 * W + j;
-        float sp, d1, d2, d3;
-        softplus_d(zp[0], sp, d1, d2, d3);
-        const float zx = zp[W], zy = zp[2 * W], zz = zp[3 * W], zl = zp[4 * W];
-        const float g0 = gp[0], gxv = gp[W], gyv = gp[2 * W], gzv = gp[3 * W], gl = gp[4 * W];
-        const float g2 = zx * zx + zy * zy + zz * zz;
-        float *o = gz + p * 5 * W + j;
-        o[0] = g0 * d1 + (gxv * zx + gyv * zy + gzv * zz) * d2 + gl * (d3 * g2 + d2 * zl);
-        o[W] = gxv * d1 + 2.0f * gl * d2 * zx;
-        o[2 * W] = gyv * d1 + 2.0f * gl * d2 * zy;
-        o[3 * W] = gzv * d1 + 2.0f * gl * d2 * zz;
-        o[4 * W] = gl * d1;
+        float o[5];
+        act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
+        float *op = gz + p * 5 * W + j;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) op[c * W] = o[c];
     }
+}
+
+// Fused forms for the tensor-core training: the activation (BWD = false) or
+// its backward (BWD = true) of a block of 16 positions (80 rows of [5 P][W])
+// x 64 units, staged in shared memory and written straight out as both BF16
+// operand images of the result (direct: rows = the 5 P rows, K = units;
+// transposed: rows = units, K = the 5 P rows), with the zero padding of both
+// images; the FP32 result is not stored.  BWD also adds the block's column
+// sums of the value rows to the bias gradient gb.  Blocks cover the rows
+// padded to a multiple of 128 (rows past 5 P are zero) and the units padded
+// to a multiple of 128 (the transposed image's rows); nbc column blocks per
+// row of blocks, linear block index.
+__device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(256) act_images_kernel(const float *__restrict__ z, const float *__restrict__ g,
+                                                         int64_t P, int W, int64_t nbc, int64_t rows_pad_d,
+                                                         int64_t kc_n_d, uint8_t *__restrict__ img_d,
+                                                         int64_t rows_pad_t, int64_t kc_n_t,
+                                                         uint8_t *__restrict__ img_t, float *__restrict__ gb) {
+    using spo_detail::kImgRows;
+    using spo_detail::kImgTileBytes;
+    __shared__ float h[80][65];
+    const int64_t br = (int64_t)blockIdx.x / nbc;
+    const int64_t p0 = br * 16, r0 = br * 80, c0 = ((int64_t)blockIdx.x - br * nbc) * 64;
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+        const int pl = e >> 6, cj = e & 63;
+        const int64_t p = p0 + pl, j = c0 + cj;
+        float o[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (p < P && j < W) {
+            if constexpr (BWD) act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
+            else act_fwd_one(z + p * 5 * W + j, W, o);
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) h[pl * 5 + c][cj] = o[c];
+    }
+    __syncthreads();
+    if constexpr (BWD) {
+        if (threadIdx.x < 64 && c0 + threadIdx.x < W) {
+            float sb = 0.0f;
+            for (int pl = 0; pl < 16; ++pl) sb += h[pl * 5][threadIdx.x];
+            atomicAdd(gb + c0 + threadIdx.x, sb);
+        }
+    }
+    const int64_t KBd = kc_n_d / 8, KBt = kc_n_t / 8;
+    for (int e = threadIdx.x; e < 80 * 8; e += 256) {   // direct: row r0 + r, K columns c0 + 8q ..
+        const int r = e >> 3, q = e & 7;
+        const int64_t row = r0 + r, kc = c0 / 8 + q;
+        if (row < rows_pad_d && kc < kc_n_d) {
+            const float *v = &h[r][8 * q];
+            uint8_t *t = img_d + (size_t)((row / kImgRows) * KBd + kc / 8) * kImgTileBytes;
+            *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), q * 8)) =
+                make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
+                           bf16x2_rn(v[6], v[7]));
+        }
+    }
+    for (int e = threadIdx.x; e < 64 * 10; e += 256) {   // transposed: row c0 + cc, K rows r0 + 8q ..
+        const int cc = e & 63, q = e >> 6;
+        const int64_t row = c0 + cc, kc = r0 / 8 + q;
+        if (row < rows_pad_t && kc < kc_n_t) {
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = h[8 * q + k][cc];
+            uint8_t *t = img_t + (size_t)((row / kImgRows) * KBt + kc / 8) * kImgTileBytes;
+            *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), (int)(kc % 8) * 8)) =
+                make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
+                           bf16x2_rn(v[6], v[7]));
+        }
+    }
+}
+
+// Both images of the activation (or, with g, of its backward) of [5 P][W];
+// gb: the bias gradient (backward only).
+cudaError_t act_images(bool bwd, const float *z, const float *g, int64_t P, int W, uint8_t *img_d,
+                       uint8_t *img_t, float *gb, cudaStream_t st) {
+    const int64_t M = 5 * P;
+    const int64_t rp_d = (M + 127) / 128 * 128, kc_d = ((int64_t)W + 63) / 64 * 8;
+    const int64_t rp_t = ((int64_t)W + 127) / 128 * 128, kc_t = (M + 63) / 64 * 8;
+    const int64_t nbr = (rp_d + 79) / 80, nbc = rp_t / 64;
+    const int64_t blocks = nbr * nbc;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (bwd)
+        act_images_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(z, g, P, W, nbc, rp_d, kc_d, img_d, rp_t, kc_t,
+                                                                  img_t, gb);
+    else
+        act_images_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(z, nullptr, P, W, nbc, rp_d, kc_d, img_d, rp_t,
+                                                                   kc_t, img_t, nullptr);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -711,34 +816,23 @@ cudaError_t ensure_images(spo_surrogate *s, int64_t M) {
     return cudaSuccess;
 }
 
-// Z [M][o] = X [M][in] W_l^T, plus b_l on the value rows.  Tensor-core form:
-// X's two images in one pass (X^T kept for the weight gradient), W's images
-// made at the start of the pass.
-cudaError_t lin_forward(spo_surrogate *s, bool tc, const float *X, int l, float *Z, int64_t M, cudaStream_t st) {
+// Z [M][o] = X [M][in] W_l^T, plus b_l on the value rows (FP32 products on
+// the CUDA cores).
+cudaError_t lin_forward(spo_surrogate *s, const float *X, int l, float *Z, int64_t M, cudaStream_t st) {
     const int in = s->widths[l], o = s->widths[l + 1];
     const float *W = s->param + s->w_off[l], *b = s->param + s->b_off[l];
-    if (!tc) return gemm(0, false, X, W, Z, b, (int)M, o, in, in, in, st);
-    cudaError_t e = spo_detail::to_bf16_images(X, M, in, in, s->ia, s->xt[l], st);
-    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->ia, s->wd[l], M, o, in, Z, b, false, st);
-    return e;
+    return gemm(0, false, X, W, Z, b, (int)M, o, in, in, in, st);
 }
 
 // dW_l [o][in] += gz [M][o]^T X [M][in] and G [M][in] = gz [M][o] W_l [o][in]
-// (G may be null: no data gradient).  Tensor-core form: gz's two images in
-// one pass, X^T and W^T from the forward pass.
-cudaError_t lin_backward(spo_surrogate *s, bool tc, const float *gz, const float *X, int l, float *G, int64_t M,
+// (FP32 products on the CUDA cores).
+cudaError_t lin_backward(spo_surrogate *s, const float *gz, const float *X, int l, float *G, int64_t M,
                          cudaStream_t st) {
     const int in = s->widths[l], o = s->widths[l + 1];
     float *dW = s->grad + s->w_off[l];
     const float *W = s->param + s->w_off[l];
-    if (!tc) {
-        cudaError_t e = gemm(2, false, gz, X, dW, nullptr, o, in, (int)M, o, in, st);
-        if (e == cudaSuccess && G) e = gemm(1, false, gz, W, G, nullptr, (int)M, in, o, o, in, st);
-        return e;
-    }
-    cudaError_t e = spo_detail::to_bf16_images(gz, M, o, o, s->ib, s->ia, st);
-    if (e == cudaSuccess) e = spo_detail::tc_gemm(s->ia, s->xt[l], o, in, M, dW, nullptr, true, st);
-    if (e == cudaSuccess && G) e = spo_detail::tc_gemm(s->ib, s->wt[l], M, in, o, G, nullptr, false, st);
+    cudaError_t e = gemm(2, false, gz, X, dW, nullptr, o, in, (int)M, o, in, st);
+    if (e == cudaSuccess) e = gemm(1, false, gz, W, G, nullptr, (int)M, in, o, o, in, st);
     return e;
 }
 
@@ -757,9 +851,21 @@ cudaError_t forward_train(spo_surrogate *s, const float *pos, int64_t P, float *
         if (e != cudaSuccess) return e;
     }
     for (int l = 0; l < s->nl; ++l) {
-        const int o = s->widths[l + 1];
+        const int in = s->widths[l], o = s->widths[l + 1];
         float *z = (l == s->nl - 1 && out) ? out : s->pre[l];
-        e = lin_forward(s, tc, s->act[l], l, z, 5 * P, st);
+        if (tc) {
+            // layer l's input images: the encoder output's made here, the
+            // others by the previous layer's fused activation
+            if (l == 0) e = spo_detail::to_bf16_images(s->act[0], 5 * P, in, in, s->ia, s->xt[0], st);
+            else e = cudaSuccess;
+            if (e == cudaSuccess)
+                e = spo_detail::tc_gemm(s->ia, s->wd[l], 5 * P, o, in, z, s->param + s->b_off[l], false, st);
+            if (e == cudaSuccess && l < s->nl - 1)
+                e = act_images(false, z, nullptr, P, o, s->ia, s->xt[l + 1], nullptr, st);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
+        e = lin_forward(s, s->act[l], l, z, 5 * P, st);
         if (e != cudaSuccess) return e;
         if (l < s->nl - 1) {
             act_fwd_kernel<<<blocks_for(P * o), 256, 0, st>>>(z, s->act[l + 1], P, o);
@@ -834,7 +940,27 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     }
     // g = gbuf[gi] is d loss / d output of layer l; the two buffers alternate
     int gi = 1;
-    for (int l = s->nl - 1; l >= 0 && e == cudaSuccess; --l) {
+    for (int l = s->nl - 1; l >= 0 && e == cudaSuccess && tc; --l) {
+        // tensor-core form: gz's two images come from the fused backward of
+        // layer l's activation (which also adds the bias gradient), or, for
+        // the output layer, from the loss gradient
+        const int in = s->widths[l], o = s->widths[l + 1];
+        float *gb = s->grad + s->b_off[l];
+        if (l < s->nl - 1) {
+            e = act_images(true, s->pre[l], s->gbuf[gi], P, o, s->ib, s->ia, gb, st);
+        } else {
+            bias_grad_kernel<<<dim3((o + 127) / 128, (unsigned)std::min<int64_t>(P, 256)), 128, 0, st>>>(
+                s->gbuf[gi], P, o, gb);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = spo_detail::to_bf16_images(s->gbuf[gi], M, o, o, s->ib, s->ia, st);
+        }
+        if (e == cudaSuccess)
+            e = spo_detail::tc_gemm(s->ia, s->xt[l], o, in, M, s->grad + s->w_off[l], nullptr, true, st);
+        if (e == cudaSuccess)   // d loss / d input of layer l
+            e = spo_detail::tc_gemm(s->ib, s->wt[l], M, in, o, s->gbuf[1 - gi], nullptr, false, st);
+        gi = 1 - gi;
+    }
+    for (int l = s->nl - 1; l >= 0 && e == cudaSuccess && !tc; --l) {
         const int o = s->widths[l + 1];
         float *gz = s->gbuf[gi];
         if (l < s->nl - 1) {   // through the softplus of layer l
@@ -849,7 +975,7 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {   // weight gradient and d loss / d input of layer l
-            e = lin_backward(s, tc, gz, s->act[l], l, s->gbuf[1 - gi], M, st);
+            e = lin_backward(s, gz, s->act[l], l, s->gbuf[1 - gi], M, st);
             gi = 1 - gi;
         }
     }

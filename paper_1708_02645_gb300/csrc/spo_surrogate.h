@@ -69,7 +69,11 @@ cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const S
 
 // BF16 tile images of GEMM operands (tiles of 128 rows x 64 K-columns in the
 // 128-byte swizzle layout, zero beyond the matrix) and the tensor-core GEMM
-// that reads them (spo_tc_gemm.cu).
+// that reads them (spo_tc_gemm.cu).  Tile (mt, kb) of an image with KB
+// K-blocks starts at byte (mt * KB + kb) * kImgTileBytes; a 16-byte chunk (8
+// K-columns) of row r sits at sw128_offset(r % kImgRows, 8 * chunk).
+constexpr int kImgRows = 128, kImgK = 64;
+constexpr uint32_t kImgTileBytes = kImgRows * kImgK * 2;
 size_t bf16_image_bytes(int64_t rows, int64_t K);
 // src: FP32 [R][C] row major, leading dimension ld.  transpose = false: the
 // image of src (rows R, K = C); true: the image of src^T (rows C, K = R).

@@ -30,8 +30,8 @@ namespace {
 
 using namespace spo_dev;
 
-constexpr int kRowsT = 128, kColsT = 64;
-constexpr uint32_t kTileBytes = kRowsT * kColsT * 2;   // 16 KB
+constexpr int kRowsT = spo_detail::kImgRows, kColsT = spo_detail::kImgK;
+constexpr uint32_t kTileBytes = spo_detail::kImgTileBytes;   // 16 KB
 constexpr int kMaxStages = 3;
 constexpr uint32_t kStageBytes = 2 * kTileBytes;       // A and B tiles
 // shared memory of a CTA with `stages` stages: the stages, then full[3],
