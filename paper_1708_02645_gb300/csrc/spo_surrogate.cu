@@ -355,13 +355,20 @@ __global__ void act_bwd_kernel(const float *__restrict__ z, const float *__restr
     }
 }
 
-// Fused forms for the tensor-core training: the activation (BWD = false) or
-// its backward (BWD = true) of a block of 16 positions (80 rows of [5 P][W])
-// x 64 units, staged in shared memory and written straight out as both BF16
-// operand images of the result (direct: rows = the 5 P rows, K = units;
-// transposed: rows = units, K = the 5 P rows), with the zero padding of both
-// images; the FP32 result is not stored.  BWD also adds the block's column
-// sums of the value rows to the bias gradient gb.  Blocks cover the rows
+struct ChannelWeights {
+    float w[5];
+};
+
+// Fused forms for the tensor-core training, over a block of 16 positions
+// (80 rows of [5 P][W]) x 64 units: MODE kActFwd, the activation of z;
+// kActBwd, its backward from z and g = d loss / d h; kLoss, the loss
+// gradient 2 w_c (z - g) / (P W) of the network output z against the target
+// g, with the loss sum_c w_c mean((z - g)^2) added to *loss.  The block's
+// result is staged in shared memory and written straight out as both BF16
+// operand images (direct: rows = the 5 P rows, K = units; transposed: rows =
+// units, K = the 5 P rows), with the zero padding of both images; the FP32
+// result is not stored.  kActBwd and kLoss also add the block's column sums
+// of the value rows to the bias gradient gb.  Blocks cover the rows
 // padded to a multiple of 128 (rows past 5 P are zero) and the units padded
 // to a multiple of 128 (the transposed image's rows); nbc column blocks per
 // row of blocks, linear block index.
@@ -370,88 +377,119 @@ __device__ __forceinline__ uint32_t bf16x2_rn(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-template <bool BWD>
+constexpr int kActFwd = 0, kActBwd = 1, kLoss = 2;
+
+template <int MODE>
 __global__ void __launch_bounds__(256) act_images_kernel(const float *__restrict__ z, const float *__restrict__ g,
-                                                         int64_t P, int W, int64_t nbc, int64_t rows_pad_d,
-                                                         int64_t kc_n_d, uint8_t *__restrict__ img_d,
-                                                         int64_t rows_pad_t, int64_t kc_n_t,
-                                                         uint8_t *__restrict__ img_t, float *__restrict__ gb) {
+                                                         int64_t P, int W, int64_t nbc, int64_t nblocks,
+                                                         int64_t rows_pad_d, int64_t kc_n_d,
+                                                         uint8_t *__restrict__ img_d, int64_t rows_pad_t,
+                                                         int64_t kc_n_t, uint8_t *__restrict__ img_t,
+                                                         float *__restrict__ gb, ChannelWeights cw, double *loss) {
     using spo_detail::kImgRows;
     using spo_detail::kImgTileBytes;
     __shared__ float h[80][65];
-    const int64_t br = (int64_t)blockIdx.x / nbc;
-    const int64_t p0 = br * 16, r0 = br * 80, c0 = ((int64_t)blockIdx.x - br * nbc) * 64;
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-        const int pl = e >> 6, cj = e & 63;
-        const int64_t p = p0 + pl, j = c0 + cj;
-        float o[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        if (p < P && j < W) {
-            if constexpr (BWD) act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
-            else act_fwd_one(z + p * 5 * W + j, W, o);
-        }
+    __shared__ double red[256];
+    const double inv = 1.0 / ((double)P * (double)W);
+    float local = 0.0f;
+    // the CTA takes blocks blockIdx.x, blockIdx.x + gridDim.x, ...
+    for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const int64_t br = blk / nbc;
+        const int64_t p0 = br * 16, r0 = br * 80, c0 = (blk - br * nbc) * 64;
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int pl = e >> 6, cj = e & 63;
+            const int64_t p = p0 + pl, j = c0 + cj;
+            float o[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (p < P && j < W) {
+                if constexpr (MODE == kActBwd) {
+                    act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
+                } else if constexpr (MODE == kLoss) {
 #pragma unroll
-        for (int c = 0; c < 5; ++c) h[pl * 5 + c][cj] = o[c];
-    }
-    __syncthreads();
-    if constexpr (BWD) {
-        if (threadIdx.x < 64 && c0 + threadIdx.x < W) {
-            float sb = 0.0f;
-            for (int pl = 0; pl < 16; ++pl) sb += h[pl * 5][threadIdx.x];
-            atomicAdd(gb + c0 + threadIdx.x, sb);
-        }
-    }
-    const int64_t KBd = kc_n_d / 8, KBt = kc_n_t / 8;
-    for (int e = threadIdx.x; e < 80 * 8; e += 256) {   // direct: row r0 + r, K columns c0 + 8q ..
-        const int r = e >> 3, q = e & 7;
-        const int64_t row = r0 + r, kc = c0 / 8 + q;
-        if (row < rows_pad_d && kc < kc_n_d) {
-            const float *v = &h[r][8 * q];
-            uint8_t *t = img_d + (size_t)((row / kImgRows) * KBd + kc / 8) * kImgTileBytes;
-            *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), q * 8)) =
-                make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
-                           bf16x2_rn(v[6], v[7]));
-        }
-    }
-    for (int e = threadIdx.x; e < 64 * 10; e += 256) {   // transposed: row c0 + cc, K rows r0 + 8q ..
-        const int cc = e & 63, q = e >> 6;
-        const int64_t row = c0 + cc, kc = r0 / 8 + q;
-        if (row < rows_pad_t && kc < kc_n_t) {
-            float v[8];
+                    for (int c = 0; c < 5; ++c) {
+                        const int64_t at = (p * 5 + c) * W + j;
+                        const float d = z[at] - g[at];
+                        o[c] = (float)(2.0 * cw.w[c] * inv) * d;
+                        local = fmaf(cw.w[c] * d, d, local);
+                    }
+                } else {
+                    act_fwd_one(z + p * 5 * W + j, W, o);
+                }
+            }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = h[8 * q + k][cc];
-            uint8_t *t = img_t + (size_t)((row / kImgRows) * KBt + kc / 8) * kImgTileBytes;
-            *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), (int)(kc % 8) * 8)) =
-                make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
-                           bf16x2_rn(v[6], v[7]));
+            for (int c = 0; c < 5; ++c) h[pl * 5 + c][cj] = o[c];
         }
+        __syncthreads();
+        if constexpr (MODE != kActFwd) {
+            if (threadIdx.x < 64 && c0 + threadIdx.x < W) {
+                float sb = 0.0f;
+                for (int pl = 0; pl < 16; ++pl) sb += h[pl * 5][threadIdx.x];
+                atomicAdd(gb + c0 + threadIdx.x, sb);
+            }
+        }
+        const int64_t KBd = kc_n_d / 8, KBt = kc_n_t / 8;
+        for (int e = threadIdx.x; e < 80 * 8; e += 256) {   // direct: row r0 + r, K columns c0 + 8q ..
+            const int r = e >> 3, q = e & 7;
+            const int64_t row = r0 + r, kc = c0 / 8 + q;
+            if (row < rows_pad_d && kc < kc_n_d) {
+                const float *v = &h[r][8 * q];
+                uint8_t *t = img_d + (size_t)((row / kImgRows) * KBd + kc / 8) * kImgTileBytes;
+                *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), q * 8)) =
+                    make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
+                               bf16x2_rn(v[6], v[7]));
+            }
+        }
+        for (int e = threadIdx.x; e < 64 * 10; e += 256) {   // transposed: row c0 + cc, K rows r0 + 8q ..
+            const int cc = e & 63, q = e >> 6;
+            const int64_t row = c0 + cc, kc = r0 / 8 + q;
+            if (row < rows_pad_t && kc < kc_n_t) {
+                float v[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = h[8 * q + k][cc];
+                uint8_t *t = img_t + (size_t)((row / kImgRows) * KBt + kc / 8) * kImgTileBytes;
+                *reinterpret_cast<uint4 *>(t + spo_dev::sw128_offset((int)(row % kImgRows), (int)(kc % 8) * 8)) =
+                    make_uint4(bf16x2_rn(v[0], v[1]), bf16x2_rn(v[2], v[3]), bf16x2_rn(v[4], v[5]),
+                               bf16x2_rn(v[6], v[7]));
+            }
+        }
+        __syncthreads();   // h is refilled by the next block
+    }
+    if constexpr (MODE == kLoss) {
+        red[threadIdx.x] = (double)local * inv;
+        __syncthreads();
+        for (int k = 128; k > 0; k >>= 1) {
+            if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) atomicAdd(loss, red[0]);
     }
 }
 
-// Both images of the activation (or, with g, of its backward) of [5 P][W];
-// gb: the bias gradient (backward only).
-cudaError_t act_images(bool bwd, const float *z, const float *g, int64_t P, int W, uint8_t *img_d,
-                       uint8_t *img_t, float *gb, cudaStream_t st) {
+// Both images of act_images_kernel<mode>'s result over [5 P][W]; gb: the
+// bias gradient (kActBwd, kLoss); cw, loss: the loss (kLoss).
+cudaError_t act_images(int mode, const float *z, const float *g, int64_t P, int W, uint8_t *img_d,
+                       uint8_t *img_t, float *gb, cudaStream_t st, ChannelWeights cw = {},
+                       double *loss = nullptr) {
     const int64_t M = 5 * P;
     const int64_t rp_d = (M + 127) / 128 * 128, kc_d = ((int64_t)W + 63) / 64 * 8;
     const int64_t rp_t = ((int64_t)W + 127) / 128 * 128, kc_t = (M + 63) / 64 * 8;
     const int64_t nbr = (rp_d + 79) / 80, nbc = rp_t / 64;
-    const int64_t blocks = nbr * nbc;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    if (bwd)
-        act_images_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(z, g, P, W, nbc, rp_d, kc_d, img_d, rp_t, kc_t,
-                                                                  img_t, gb);
+    const int64_t nblocks = nbr * nbc;
+    const unsigned grid = (unsigned)std::min<int64_t>(nblocks, 152 * 8);
+    if (mode == kActBwd)
+        act_images_kernel<kActBwd><<<grid, 256, 0, st>>>(z, g, P, W, nbc, nblocks, rp_d, kc_d, img_d, rp_t, kc_t,
+                                                         img_t, gb, cw, loss);
+    else if (mode == kLoss)
+        act_images_kernel<kLoss><<<grid, 256, 0, st>>>(z, g, P, W, nbc, nblocks, rp_d, kc_d, img_d, rp_t, kc_t,
+                                                       img_t, gb, cw, loss);
     else
-        act_images_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(z, nullptr, P, W, nbc, rp_d, kc_d, img_d, rp_t,
-                                                                   kc_t, img_t, nullptr);
+        act_images_kernel<kActFwd><<<grid, 256, 0, st>>>(z, nullptr, P, W, nbc, nblocks, rp_d, kc_d, img_d, rp_t,
+                                                         kc_t, img_t, nullptr, cw, loss);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // loss, bias gradient, Adam, sampling, quantisation
 // ---------------------------------------------------------------------------
-struct ChannelWeights {
-    float w[5];
-};
 
 // g = 2 w_c (out - target) / (P N) in FP32; the loss sum_c w_c mean(d^2)
 // is summed per thread in FP32, per block and across blocks in FP64.
@@ -861,7 +899,7 @@ cudaError_t forward_train(spo_surrogate *s, const float *pos, int64_t P, float *
             if (e == cudaSuccess)
                 e = spo_detail::tc_gemm(s->ia, s->wd[l], 5 * P, o, in, z, s->param + s->b_off[l], false, st);
             if (e == cudaSuccess && l < s->nl - 1)
-                e = act_images(false, z, nullptr, P, o, s->ia, s->xt[l + 1], nullptr, st);
+                e = act_images(kActFwd, z, nullptr, P, o, s->ia, s->xt[l + 1], nullptr, st);
             if (e != cudaSuccess) return e;
             continue;
         }
@@ -931,7 +969,7 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     float *out = s->gbuf[0];   // network output [P][5][N] (gbuf holds max width >= N columns)
     cudaError_t e = forward_train(s, pos, P, out, st, tc);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->dacc, 0, sizeof(double), st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !tc) {
         const int vec = (N % 4 == 0 && aligned16(out) && aligned16(target) && aligned16(s->gbuf[1])) ? 1 : 0;
         const int64_t per_ch = vec ? P * (N / 4) : P * N;
         const unsigned bx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((per_ch + 255) / 256, 152 * 2));
@@ -946,14 +984,10 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
         // the output layer, from the loss gradient
         const int in = s->widths[l], o = s->widths[l + 1];
         float *gb = s->grad + s->b_off[l];
-        if (l < s->nl - 1) {
-            e = act_images(true, s->pre[l], s->gbuf[gi], P, o, s->ib, s->ia, gb, st);
-        } else {
-            bias_grad_kernel<<<dim3((o + 127) / 128, (unsigned)std::min<int64_t>(P, 256)), 128, 0, st>>>(
-                s->gbuf[gi], P, o, gb);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = spo_detail::to_bf16_images(s->gbuf[gi], M, o, o, s->ib, s->ia, st);
-        }
+        if (l < s->nl - 1)
+            e = act_images(kActBwd, s->pre[l], s->gbuf[gi], P, o, s->ib, s->ia, gb, st);
+        else   // the output layer: loss, its gradient and the bias gradient in one pass
+            e = act_images(kLoss, out, target, P, o, s->ib, s->ia, gb, st, cw, s->dacc);
         if (e == cudaSuccess)
             e = spo_detail::tc_gemm(s->ia, s->xt[l], o, in, M, s->grad + s->w_off[l], nullptr, true, st);
         if (e == cudaSuccess)   // d loss / d input of layer l
