@@ -127,3 +127,37 @@ def test_one_call_eval_batch(spo_lib, small_set):
         if p.shape[0] == 0:
             continue
         assert t.equal(o, sets[k].eval(p, "vgh"))
+
+
+def test_crowd_full_size_graph(spo_lib, oracle_lib):
+    """The benchmark's crowd in its launch form: 3 sets (32^3 x 64, 48^3 x
+    192, 64^3 x 384 orbitals), 512 walkers of 64..768 electrons, VGH through
+    one recorded graph.  Every walker equals its own spo_eval bit for bit, and
+    a seeded sample of positions of 6 walkers matches the FP64 oracle."""
+    t = torch()
+    cr = inputs.CROWD
+    coefs = [cr.make_coefs(k, np.float32) for k in range(len(cr.sets))]
+    sets = [spo_lib.OrbitalSet(c) for c in coefs]
+    sizes, which = cr.sizes(), cr.set_of_walker()
+    items = []
+    for w in range(cr.walkers):
+        k = int(which[w])
+        p = t.from_numpy(cr.make_positions(w, int(sizes[w]))).cuda()
+        o = t.full(sets[k].out_shape(p.shape[0], "vgh"), float("nan"), device="cuda")
+        items.append((k, p, o))
+    with spo_lib.Batch(sets, int(sizes.sum()), cr.walkers) as b:
+        b.graph(items, "vgh")
+        b.launch()
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    for k, p, o in items:
+        assert t.equal(o, sets[k].eval(p, "vgh"))
+    for w in (0, 1, 2, 257, 258, 511):
+        k, p, o = items[w]
+        idx = np.sort(np.unique((inputs.uniform01(500 + w, 48) * p.shape[0]).astype(np.int64)))
+        pn = p.cpu().numpy().astype(np.float64)[idx]
+        vals = coefs[k].astype(np.float64)
+        assert_kernel_parity(o.cpu().numpy()[idx], oracle.spo_eval(vals, pn, 2),
+                             oracle.condition(vals, pn, 2), 2, f"crowd walker {w}")
+    for s in sets:
+        s.close()

@@ -94,3 +94,22 @@ def test_ratio_rejects_bad_arguments(spo_lib):
             s.eval_ratio(pos, t.zeros((10, 16), device="cuda"))
         with pytest.raises(spo_lib.SpoError, match="nrows < P"):
             s.eval_ratio(pos, t.zeros((4, 32), device="cuda"))
+
+
+def test_ratio_nio64_full_batch_sampled(spo_lib, oracle_lib):
+    """The benchmark's ratio call: all 98,304 positions of the NiO-64-shaped
+    workload against 384 orbitals in one launch (brick path, fused epilogue),
+    one random row of A^-1 per position; a seeded sample of 1024 ratios
+    against the oracle."""
+    t = torch()
+    cfg = inputs.NIO64
+    c = cfg.make_coefs(np.float32)
+    pos = cfg.make_positions()
+    P = pos.shape[0]
+    rows = (2.0 * inputs.uniform01(65, P * cfg.N) - 1.0).astype(np.float32).reshape(P, cfg.N)
+    with spo_lib.OrbitalSet(c) as s:
+        got = s.eval_ratio(t.from_numpy(pos).cuda(), t.from_numpy(rows).cuda())
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    sample = np.sort(np.unique((inputs.uniform01(66, 1024) * P).astype(np.int64)))
+    check(got.cpu().numpy()[sample], c, pos[sample], rows[sample], None)
