@@ -542,8 +542,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-VARIANTS = ("all", "storage", "ratio", "autotune", "crowd", "surrogate", "surrogate_specified", "prefilter",
-            "nio32")
+VARIANTS = ("all", "storage", "ratio", "nlpp", "autotune", "crowd", "surrogate", "surrogate_specified",
+            "prefilter", "nio32")
 
 
 def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
@@ -576,6 +576,8 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
         res["f32_table_bytes"] = s32.footprint()
     if want("ratio"):
         res["ratio_fused_v"] = measure_ratio(cfg, s32, pos, steps)
+    if want("nlpp") and cfg.name == inputs.NIO64.name:
+        res["nlpp_ratio"] = measure_nlpp(cfg, s32, pos.device, steps)
     if want("autotune"):
         res["autotune"] = s32.autotune(kind, pos.shape[0])
         configure(s32, args)   # back to the command line's tuning
@@ -621,6 +623,40 @@ def measure_ratio(cfg, s32, pos, steps):
             "ratios_per_s": P / (r_ms * 1e-3), "ms_per_step": round(r_ms, 5),
             "what": "spo_eval_ratio: V of all orbitals dotted with an A^-1 row per position, "
                     "values not stored"}
+
+
+def measure_nlpp(cfg, s32, dev, steps):
+    """Determinant ratios at the non-local pseudopotential quadrature points
+    of 128 walkers x 768 electrons (12 points per electron within r_cut of an
+    ion, 64 ions), one A^-1 row per electron shared by its points."""
+    import torch
+    nl = inputs.NLPP
+    pts, row_of = nl.make_points()
+    Q = pts.shape[0]
+    rows = (2.0 * inputs.uniform01(nl.seed + 2, nl.n_electrons * cfg.N) - 1.0).astype(np.float32)
+    rows = torch.from_numpy(rows.reshape(nl.n_electrons, cfg.N)).to(dev)
+    q = torch.from_numpy(pts).to(dev)
+    ro = torch.from_numpy(row_of).to(dev)
+    ratio = torch.empty((Q,), device=dev)
+    for _ in range(3):
+        s32.eval_ratio(q, rows, ro, ratio=ratio)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        s32.eval_ratio(q, rows, ro, ratio=ratio)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    g = np.asarray(cfg.grid)
+    cells = np.minimum((pts.astype(np.float64) * g).astype(np.int64), g - 1) // 4
+    nb = -(-g // 4)
+    occupied = len(np.unique((cells[:, 0] * nb[1] + cells[:, 1]) * nb[2] + cells[:, 2]))
+    return {"workload": nl.name, "points": Q, "electrons_near_ions": Q // 12,
+            "bricks_occupied": f"{occupied} of {int(nb.prod())}",
+            "value": Q * cfg.N / (ms * 1e-3), "unit": "evals/s", "ratios_per_s": Q / (ms * 1e-3),
+            "ms_per_step": round(ms, 5),
+            "what": "spo_eval_ratio at the 12-point quadrature points, row_of = electron"}
 
 
 def measure_prefilter(cfg):

@@ -193,3 +193,67 @@ class CrowdConfig:
 
 
 CROWD = CrowdConfig()
+
+
+def icosahedron_directions() -> np.ndarray:
+    """The 12 unit vectors to the vertices of a regular icosahedron: the
+    cyclic permutations of (0, +-1, +-g), g the golden ratio, normalised (the
+    12-point rule for angular integrals over the sphere)."""
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    v = []
+    for s1 in (1.0, -1.0):
+        for s2 in (1.0, -1.0):
+            v += [(0.0, s1, s2 * g), (s1, s2 * g, 0.0), (s2 * g, 0.0, s1)]
+    v = np.asarray(v)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def random_rotations(seed: int, n: int) -> np.ndarray:
+    """n rotation matrices [n, 3, 3], uniform on SO(3): unit quaternions from
+    normalised 4-D Gaussian vectors."""
+    q = normal(seed, 4 * n).reshape(n, 4)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)], axis=1),
+        np.stack([2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)], axis=1),
+        np.stack([2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], axis=1)], axis=1)
+
+
+@dataclass(frozen=True)
+class NlppConfig:
+    """Quadrature points of the non-local pseudopotential for a batch of
+    walkers (Sec. 3: an angular quadrature on a sphere around each ion, one
+    determinant ratio per point).  Ions sit on an edge^3 lattice of the unit
+    cube; every electron within r_cut of its nearest ion contributes the 12
+    icosahedron points on the sphere through it about that ion, turned by a
+    random rotation; each point's row of A^-1 is its electron's."""
+    name: str = "nlpp_nio64_12pt"
+    ion_edge: int = 4            # 64 ions, as in the 64-atom NiO cell
+    r_cut: float = 0.09          # reduced units (about 1.5 bohr in a 16.7 bohr cell)
+    walkers: int = 128
+    electrons: int = 768
+    seed: int = SEED_BASE + 5
+
+    @property
+    def n_electrons(self) -> int:
+        return self.walkers * self.electrons
+
+    def make_points(self):
+        """(points [Q, 3] FP32 in [0, 1), row_of [Q] int32 electron index)."""
+        e = uniform_positions(self.n_electrons, self.seed).astype(np.float64)
+        a = float(self.ion_edge)
+        ion = np.round(e * a) / a                 # nearest lattice site (periodic image)
+        d = e - ion
+        r = np.linalg.norm(d, axis=1)
+        near = np.nonzero(r < self.r_cut)[0]
+        rot = random_rotations(self.seed + 1, len(near))
+        dirs = np.einsum("nij,kj->nki", rot, icosahedron_directions())      # [n, 12, 3]
+        pts = ion[near, None, :] + r[near, None, None] * dirs
+        pts = np.mod(pts, 1.0).reshape(-1, 3).astype(np.float32)
+        pts[pts >= np.float32(1.0)] = np.float32(0.0)
+        row_of = np.repeat(near.astype(np.int32), 12)
+        return pts, row_of
+
+
+NLPP = NlppConfig()

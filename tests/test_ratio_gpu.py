@@ -113,3 +113,22 @@ def test_ratio_nio64_full_batch_sampled(spo_lib, oracle_lib):
         assert spo_lib.device_status() == 0
     sample = np.sort(np.unique((inputs.uniform01(66, 1024) * P).astype(np.int64)))
     check(got.cpu().numpy()[sample], c, pos[sample], rows[sample], None)
+
+
+def test_ratio_nlpp_quadrature_batch_sampled(spo_lib, oracle_lib):
+    """Ratios at the non-local pseudopotential quadrature points of the
+    NiO-64-shaped crowd (12 points per electron within r_cut of one of 64
+    ions: clustered positions, half of the bricks empty), the points of an
+    electron sharing its row of A^-1; a seeded sample against the oracle."""
+    t = torch()
+    cfg, nl = inputs.NIO64, inputs.NLPP
+    c = cfg.make_coefs(np.float32)
+    pts, row_of = nl.make_points()
+    rows = (2.0 * inputs.uniform01(nl.seed + 2, nl.n_electrons * cfg.N) - 1.0).astype(np.float32)
+    rows = rows.reshape(nl.n_electrons, cfg.N)
+    with spo_lib.OrbitalSet(c) as s:
+        got = s.eval_ratio(t.from_numpy(pts).cuda(), t.from_numpy(rows).cuda(), t.from_numpy(row_of).cuda())
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+    sample = np.sort(np.unique((inputs.uniform01(67, 1024) * len(pts)).astype(np.int64)))
+    check(got.cpu().numpy()[sample], c, pts[sample], rows, row_of[sample])
