@@ -343,7 +343,11 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  *   for them (the spline kernels), and takes one Adam step on sum_c w_c
  *   mean((out_c - target_c)^2).  channel_weights = 5 floats (V, Gx, Gy, Gz,
  *   L) or NULL for 1 / mean(target_c^2) of the first batch.  The teacher must
- *   have the same N.  Synchronous; refreshes the inference copies.
+ *   have the same N.  The samples of several consecutive steps (enough for
+ *   about 32 positions per brick of the teacher, at most 1 GiB of teacher
+ *   values) are drawn and evaluated in one launch and held on the device
+ *   until used; the results equal step-by-step draws.  Synchronous;
+ *   refreshes the inference copies.
  * spo_surrogate_eval(s, kind, pos, P, out, precision, stream): kind V or
  *   VGL; precision 0 evaluates the FP32 master parameters (CUDA cores),
  *   precision 1 the inference copies (FP16 grid, BF16 weights and
