@@ -86,7 +86,7 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def resolve_algo(name: str, s, P: int) -> str:
+def resolve_algo(name: str, s, P: int, kind: str) -> str:
     """The strategy "auto" picks for this set and batch (mirrors the library's
     rule, so that the launch count and the timed kernel are known)."""
     if name != "auto":
@@ -95,11 +95,12 @@ def resolve_algo(name: str, s, P: int) -> str:
     nbins = 1
     for n in g:
         nbins *= (n + 3) // 4
-    if P < 1024:
+    if P < 1024 or 2 * P < 3 * nbins:
         return "gather"
-    if s.info()["Np"] >= 32 and P >= nbins:
+    brick_from = {"vgh": 3, "vgl": 8, "v": 12}[kind]
+    if s.info()["Np"] >= 32 and P >= brick_from * nbins:
         return "brick"
-    return "sorted_gather" if P >= 4 * nbins else "gather"
+    return "sorted_gather"
 
 
 def recorded_traffic(workload: str, storage: str, kind: str, tuning: str):
@@ -433,7 +434,7 @@ def run_ours(args):
     configure(s, args)
     stream = torch.cuda.current_stream()
 
-    algo = resolve_algo(args.algo, s, P)
+    algo = resolve_algo(args.algo, s, P, kind)
     for _ in range(args.warmup):
         s.eval(pos, kind, out=out, algo=algo)
     torch.cuda.synchronize()
@@ -595,7 +596,7 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
             configure(sv, args)
             for kd in ("v", "vgl", "vgh"):
                 o = torch.empty(sv.out_shape(n32.P, kd), dtype=torch.float32, device=pos.device)
-                a = resolve_algo(args.algo, sv, n32.P)
+                a = resolve_algo(args.algo, sv, n32.P, kd)
                 step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
                 res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
                                            "ms_per_step": round(step_ms, 5), "algo": a}

@@ -163,6 +163,11 @@ spo_status spo_eval(const spo_set *set, spo_kind kind, const float *pos, int64_t
  * stream are ordered by the stream; calls on different streams use
  * different scratch areas.  A call that allocates scratch synchronises the
  * device and cannot be captured in a CUDA graph: call spo_reserve first.
+ * SPO_ALGO_AUTO takes the set's tuned strategy (spo_autotune) for batches
+ * within 4x of the tuned size, else decides by the mean number of positions
+ * per brick r = P / bricks: GATHER for P < 1024 or r < 1.5, BRICK from r = 3
+ * (VGH), 8 (VGL) or 12 (V) when the set has 32+ padded orbitals, and
+ * SORTED_GATHER in between (crossovers measured on GB300).
  */
 spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int64_t P,
                        float *out, void *stream, spo_algo algo);

@@ -139,13 +139,20 @@ spo_status ensure_floats(float **buf, size_t *cap, size_t need) {
     return SPO_OK;
 }
 
-spo_algo choose_algo(const spo_set *s, int64_t P) {
+// The strategy AUTO takes (without a tuned choice), by the mean number of
+// positions per brick r = P / bricks.  Measured crossovers (NiO-64 and
+// NiO-32 shapes, FP32): below r = 1.5 the gather kernel in input order wins
+// (no binning, little reuse to gain); a staged block pays for itself once a
+// brick holds enough positions to amortise it against the arithmetic: r = 3
+// for VGH (656 flop per evaluation), 8 for VGL, 12 for V (the kernel whose
+// cost is shared-memory reads); in between, the gather kernel in binned
+// order (L2 reuse without staging) is fastest.
+spo_algo choose_algo(const spo_set *s, spo_kind kind, int64_t P) {
     const int64_t nbins = (int64_t)s->nbx * s->nby * s->nbz;
-    if (P >= INT_MAX || P < 1024) return SPO_ALGO_GATHER;
-    // a staged block pays off once a brick holds positions on average
-    if (s->has_block_map && P >= nbins) return SPO_ALGO_BRICK;
-    if (P >= 4 * nbins) return SPO_ALGO_SORTED_GATHER;
-    return SPO_ALGO_GATHER;
+    if (P >= INT_MAX || P < 1024 || 2 * P < 3 * nbins) return SPO_ALGO_GATHER;
+    const int64_t brick_from = kind == SPO_KIND_VGH ? 3 : (kind == SPO_KIND_VGL ? 8 : 12);
+    if (s->has_block_map && P >= brick_from * nbins) return SPO_ALGO_BRICK;
+    return SPO_ALGO_SORTED_GATHER;
 }
 
 // Queue the binning of pos into the scratch of `stream`.  Caller holds set->mu.
@@ -197,7 +204,7 @@ spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64
         const int64_t tp = set->tuned_P[k];
         algo = (set->tuned_algo[k] != 0 && P * 4 >= tp && P <= tp * 4)
                    ? static_cast<spo_algo>(set->tuned_algo[k])
-                   : choose_algo(set, P);
+                   : choose_algo(set, kind, P);
     }
     if (algo == SPO_ALGO_GATHER) {
         cudaError_t e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
@@ -448,7 +455,9 @@ spo_status spo_eval_ratio(const spo_set *set, const float *pos, int64_t P, const
     std::lock_guard<std::mutex> lock(s->mu);
     spo_detail::RatioArgs ra{rows, row_of, nrows, ld, nullptr, P};
     cudaError_t e;
-    if (s->has_block_map && choose_algo(s, P) == SPO_ALGO_BRICK) {
+    // the fused epilogue once bricks hold a position on average (the other
+    // path is the input-order gather and a separate dot product)
+    if (s->has_block_map && P >= 1024 && P >= (int64_t)s->nbx * s->nby * s->nbz) {
         spo_detail::Workspace *w = nullptr;
         if ((st = bin_queue(s, pos, P, cs, &w)) != SPO_OK) return st;
         const int ntiles = spo_detail::brick_tiles_of(s);
