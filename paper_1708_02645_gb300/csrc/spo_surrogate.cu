@@ -396,23 +396,39 @@ __global__ void __launch_bounds__(256) act_images_kernel(const float *__restrict
     for (int64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
         const int64_t br = blk / nbc;
         const int64_t p0 = br * 16, r0 = br * 80, c0 = (blk - br * nbc) * 64;
-        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+        // 16 x 64 (position, unit) pairs, 4 per thread: all their loads are
+        // issued before any of their arithmetic
+        float zin[4][5], gin[4][5];
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int e = threadIdx.x + 256 * it;
+            const int64_t p = p0 + (e >> 6), j = c0 + (e & 63);
+            const bool ok = p < P && j < W;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const int64_t at = (p * 5 + c) * W + j;
+                zin[it][c] = ok ? __ldg(z + at) : 0.0f;
+                if constexpr (MODE != kActFwd) gin[it][c] = ok ? __ldg(g + at) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int e = threadIdx.x + 256 * it;
             const int pl = e >> 6, cj = e & 63;
-            const int64_t p = p0 + pl, j = c0 + cj;
+            const bool ok = p0 + pl < P && c0 + cj < W;
             float o[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (p < P && j < W) {
+            if (ok) {
                 if constexpr (MODE == kActBwd) {
-                    act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
+                    act_bwd_one(zin[it], gin[it], 1, o);
                 } else if constexpr (MODE == kLoss) {
 #pragma unroll
                     for (int c = 0; c < 5; ++c) {
-                        const int64_t at = (p * 5 + c) * W + j;
-                        const float d = z[at] - g[at];
+                        const float d = zin[it][c] - gin[it][c];
                         o[c] = (float)(2.0 * cw.w[c] * inv) * d;
                         local = fmaf(cw.w[c] * d, d, local);
                     }
                 } else {
-                    act_fwd_one(z + p * 5 * W + j, W, o);
+                    act_fwd_one(zin[it], 1, o);
                 }
             }
 #pragma unroll

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) to_image2_kernel(const float *__restrict_
     const int64_t br = (int64_t)blockIdx.x / nbc;
     const int64_t r0 = br * 64, c0 = ((int64_t)blockIdx.x - br * nbc) * 64;
     const int tcol = threadIdx.x & 63, trow = threadIdx.x >> 6;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < 16; ++k) {
         const int r = trow + 4 * k;
         const int64_t gr = r0 + r, gc = c0 + tcol;
