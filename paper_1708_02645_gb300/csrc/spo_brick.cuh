@@ -8,17 +8,21 @@
 // are then evaluated from shared memory (2 or 4 orbitals per thread, so a
 // corner row is one conflict-free 8- or 16-byte shared load per thread for
 // FP32, 4 or 8 bytes for BF16/FP16); positions are read as sorted
-// (x, y, z, index) records written by the binning, one round ahead; the
-// z -> y -> x reduction and
-// its FMA order are those of the gather kernel (spo_device.cuh), and outputs
-// are scattered back to each position's own rows with streaming stores.
+// (x, y, z, index) records written by the binning, one round ahead; each
+// position's 36 weights are formed once by three lanes of its group and
+// shared through a slot in shared memory (spo_device.cuh,
+// stage_axis_weights); the z -> y -> x reduction and its FMA order are
+// those of the gather kernel (spo_device.cuh), and outputs are scattered
+// back to each position's own rows with streaming stores.  With 32-orbital
+// tiles and at least two bricks along z, a CTA takes a z-adjacent pair of
+// bricks instead (PAIR: one 7 x 7 x 11-node box).
 //
 // Against the gather kernel, the table bytes moved from L2 to the SMs drop
 // from 64 rows per evaluation to 343 rows per (brick, tile), and the L2 sees
 // neighbouring bricks' blocks in launch order, so DRAM reads approach one
-// pass over the table per batch.  Two (64-orbital tiles) or four
-// (32-orbital tiles) CTAs run per SM, so one CTA's copy overlaps the
-// others' arithmetic.
+// pass over the table per batch.  Two (64-orbital tiles), three (brick
+// pairs) or four (32-orbital tiles) CTAs run per SM, so one CTA's copy
+// overlaps the others' arithmetic.
 //
 // The wait on the copy is bounded (2 s of %globaltimer): if it ever gives up,
 // the CTA sets bit 0 of the device status word and returns.
