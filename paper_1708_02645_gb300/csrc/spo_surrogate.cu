@@ -294,12 +294,19 @@ gemm_v4_kernel(const float *__restrict__ A, const float *__restrict__ B, float *
 // ---------------------------------------------------------------------------
 // softplus with channels
 // ---------------------------------------------------------------------------
+// softplus(z) and its first three derivatives: sigma, sigma (1 - sigma),
+// sigma (1 - sigma) (1 - 2 sigma).  One exponential e = exp(-|z|) serves the
+// softplus and both tails of the sigmoid: with r = 1 / (1 + e), sigma is r
+// for z >= 0 and e r below, and 1 - sigma the other one (so 1 - sigma is
+// formed without cancellation for large z).
 __device__ __forceinline__ void softplus_d(float z, float &sp, float &d1, float &d2, float &d3) {
-    sp = fmaxf(z, 0.0f) + log1pf(expf(-fabsf(z)));
-    const float sg = 1.0f / (1.0f + expf(-z));
-    d1 = sg;
-    d2 = sg * (1.0f - sg);
-    d3 = d2 * (1.0f - 2.0f * sg);
+    const float e = expf(-fabsf(z));
+    const float r = 1.0f / (1.0f + e), er = e * r;
+    sp = fmaxf(z, 0.0f) + log1pf(e);
+    const float s1 = z >= 0.0f ? r : er, s0 = z >= 0.0f ? er : r;
+    d1 = s1;
+    d2 = s1 * s0;
+    d3 = d2 * (s0 - s1);
 }
 
 // h = the five channels of softplus(z) for one unit: value, gradient, Laplacian
