@@ -515,7 +515,7 @@ def run_ours(args):
         "config": dict(base_config(cfg, storage, kind, P), algo=algo, brick_vec=args.brick_vec,
                        brick_tile=args.brick_tile, brick_schedule=args.brick_schedule),
         "roofline": roofline, "e2e": e2e,
-        "gpu_launches": args.steps * (1 if algo == "gather" else 4),
+        "gpu_launches": args.steps * (1 if algo == "gather" else 3),   # binning: count (+ scan) and scatter
         "clocks": sampler.summary(),
     }
     if world > 1:

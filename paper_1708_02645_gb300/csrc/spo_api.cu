@@ -105,7 +105,10 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
         w->counts = w->offsets = w->keys = w->slots = w->perm = nullptr;
         w->sorted = nullptr;
         w->cap_positions = w->cap_bins = 0;
-        if (cudaMalloc(&w->counts, sizeof(int) * cb) != cudaSuccess ||
+        // counts: nbins + 1 ints (the last one the count kernel's ticket),
+        // zero between calls (the count kernel clears what it used)
+        if (cudaMalloc(&w->counts, sizeof(int) * (cb + 1)) != cudaSuccess ||
+            cudaMemset(w->counts, 0, sizeof(int) * (cb + 1)) != cudaSuccess ||
             cudaMalloc(&w->offsets, sizeof(int) * (cb + 1)) != cudaSuccess ||
             cudaMalloc(&w->keys, sizeof(int) * cp) != cudaSuccess ||
             cudaMalloc(&w->slots, sizeof(int) * cp) != cudaSuccess ||

@@ -3,10 +3,15 @@
 // table, and the gather kernel can visit positions in spatial order.
 //
 //   1. bin_count_kernel:  key = brick of the position's cell; slot = rank of
-//                         the position within its brick (atomic counter)
-//   2. bin_scan_kernel:   offsets = exclusive prefix sum of the counts
-//   3. bin_scatter_kernel: perm[offsets[key] + slot] = position index, and
+//                         the position within its brick (atomic counter);
+//                         the last block to finish (a ticket counter after a
+//                         fence) turns the counts into offsets = their
+//                         exclusive prefix sum and zeroes the counts (and
+//                         the ticket) for the next call, so no block waits
+//                         on another and no memset is needed
+//   2. bin_scatter_kernel: perm[offsets[key] + slot] = position index, and
 //                         the position with its index in the same sorted slot
+// (bin_scan_kernel is the stand-alone scan, used by the crowd binning.)
 //
 // The order inside a brick depends on atomic arrival order; every output of
 // a position depends only on that position, so results are unaffected.
@@ -19,9 +24,77 @@ namespace {
 using namespace spo_dev;
 using spo_detail::kBrick;
 
-__global__ void bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis gy,
-                                 GridAxis gz, int nby, int nbz, int *__restrict__ counts,
-                                 int *__restrict__ keys, int *__restrict__ slots) {
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kCountThreads = 256;
+
+// Exclusive scan of counts[0..n) into offsets[0..n] by one block of THREADS
+// threads, in chunks of THREADS * kScanItems with a running carry; with
+// CLEAR the counts are zeroed once read.  Reads go to L2 (counts were
+// updated by other blocks' atomics).
+template <int THREADS, bool CLEAR>
+__device__ void block_scan_counts(int *counts, int *offsets, int n) {
+    __shared__ int warp_sums[THREADS / 32];
+    __shared__ int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += THREADS * kScanItems) {
+        int v[kScanItems];
+        int sum = 0;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int i = base + tid * kScanItems + k;
+            v[k] = i < n ? __ldcg(counts + i) : 0;
+            if (CLEAR && i < n) counts[i] = 0;
+            sum += v[k];
+        }
+        int incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        if (lane == 31) warp_sums[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const int w = lane < THREADS / 32 ? warp_sums[lane] : 0;
+            int wi = w;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, d);
+                if (lane >= d) wi += y;
+            }
+            if (lane < THREADS / 32) warp_sums[lane] = wi - w;   // exclusive prefix of warp totals
+        }
+        __syncthreads();
+        int run = carry_s + warp_sums[warp] + incl - sum;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            const int i = base + tid * kScanItems + k;
+            if (i < n) offsets[i] = run;
+            run += v[k];
+        }
+        __syncthreads();
+        if (tid == THREADS - 1) carry_s = run;   // last thread holds the chunk total
+        __syncthreads();
+    }
+    if (tid == 0) offsets[n] = carry_s;
+}
+
+// Exclusive scan of counts[0..n) into offsets[0..n], one block (the crowd
+// binning's counts are cleared by its own memset).
+__global__ void __launch_bounds__(kScanThreads)
+bin_scan_kernel(int *__restrict__ counts, int *__restrict__ offsets, int n) {
+    block_scan_counts<kScanThreads, false>(counts, offsets, n);
+}
+
+// counts[0..nbins) must be zero and counts[nbins] (the ticket) zero on entry;
+// both are zero again on exit, with offsets[0..nbins] written.
+__global__ void __launch_bounds__(kCountThreads)
+bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis gy, GridAxis gz, int nby,
+                 int nbz, int nbins, int *__restrict__ counts, int *__restrict__ offsets,
+                 int *__restrict__ keys, int *__restrict__ slots) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         int cx, cy, cz;
@@ -33,62 +106,18 @@ __global__ void bin_count_kernel(const float *__restrict__ pos, int64_t P, GridA
         keys[p] = key;
         slots[p] = atomicAdd(counts + key, 1);
     }
-}
-
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 4;
-
-// Exclusive scan of counts[0..n) into offsets[0..n]; one block, looping over
-// chunks of kScanThreads * kScanItems with a running carry.
-__global__ void __launch_bounds__(kScanThreads)
-bin_scan_kernel(const int *__restrict__ counts, int *__restrict__ offsets, int n) {
-    __shared__ int warp_sums[kScanThreads / 32];
-    __shared__ int carry_s;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0;
+    // the last block to finish scans (no block waits for another)
+    __shared__ int last;
     __syncthreads();
-    for (int base = 0; base < n; base += kScanThreads * kScanItems) {
-        int v[kScanItems];
-        int sum = 0;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int i = base + tid * kScanItems + k;
-            v[k] = i < n ? counts[i] : 0;
-            sum += v[k];
-        }
-        // inclusive scan of the per-thread sums within the warp
-        int incl = sum;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        if (lane == 31) warp_sums[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int w = warp_sums[lane];
-            int wi = w;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, wi, d);
-                if (lane >= d) wi += y;
-            }
-            warp_sums[lane] = wi - w;   // exclusive prefix of warp totals
-        }
-        __syncthreads();
-        const int carry = carry_s;
-        int run = carry + warp_sums[warp] + incl - sum;
-#pragma unroll
-        for (int k = 0; k < kScanItems; ++k) {
-            const int i = base + tid * kScanItems + k;
-            if (i < n) offsets[i] = run;
-            run += v[k];
-        }
-        __syncthreads();
-        if (tid == kScanThreads - 1) carry_s = run;   // last thread holds the chunk total
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's counts before its ticket
+        last = atomicAdd(counts + nbins, 1) == (int)gridDim.x - 1;
     }
-    if (tid == 0) offsets[n] = carry_s;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();   // every block's counts are visible to this one
+    block_scan_counts<kCountThreads, true>(counts, offsets, nbins);
+    if (threadIdx.x == 0) counts[nbins] = 0;
 }
 
 __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
@@ -108,21 +137,21 @@ __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__r
 namespace spo_detail {
 
 cudaError_t launch_scan(const int *counts, int *offsets, int n, cudaStream_t stream) {
-    bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(counts, offsets, n);
+    // the stand-alone scan only reads the counts
+    bin_scan_kernel<<<1, kScanThreads, 0, stream>>>(const_cast<int *>(counts), offsets, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int nbx, int nby,
                        int nbz, Workspace &w, cudaStream_t stream) {
+    // w.counts holds nbins + 1 zeroed ints (the counts and the ticket); the
+    // count kernel leaves them zeroed
     const int nbins = nbx * nby * nbz;
-    cudaError_t e = cudaMemsetAsync(w.counts, 0, sizeof(int) * (size_t)nbins, stream);
-    if (e != cudaSuccess) return e;
-    const int threads = 256;
-    const int blocks = (int)std::min<int64_t>((P + threads - 1) / threads, 152 * 16);
-    bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, grid_axis(nx), grid_axis(ny),
-                                                     grid_axis(nz), nby, nbz, w.counts, w.keys,
-                                                     w.slots);
-    e = launch_scan(w.counts, w.offsets, nbins, stream);
+    const int threads = kCountThreads;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P + threads - 1) / threads, 152 * 16));
+    bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, grid_axis(nx), grid_axis(ny), grid_axis(nz), nby,
+                                                     nbz, nbins, w.counts, w.offsets, w.keys, w.slots);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bin_scatter_kernel<<<blocks, threads, 0, stream>>>(pos, w.keys, w.slots, w.offsets, w.perm,
                                                        w.sorted, P);

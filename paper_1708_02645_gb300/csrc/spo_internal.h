@@ -23,7 +23,7 @@ constexpr int kBlockEdge = kBrick + 3;
 // the positions themselves in that order (x, y, z, original index as bits).
 struct Workspace {
     cudaStream_t stream = nullptr;
-    int *counts = nullptr;    // [nbins]
+    int *counts = nullptr;    // [nbins + 1], zero between binnings (the last: a ticket)
     int *offsets = nullptr;   // [nbins + 1]
     int *keys = nullptr;      // [P]
     int *slots = nullptr;     // [P]

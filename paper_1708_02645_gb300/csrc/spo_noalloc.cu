@@ -38,7 +38,7 @@ constexpr size_t kMaxBricks = SPO_NOALLOC_MAX_BRICKS;
 // [sorted: kMaxPositions float4], every part starting on a 256-byte boundary
 constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 constexpr size_t kCountsOff = 0;
-constexpr size_t kOffsetsOff = kCountsOff + align256(kMaxBricks * sizeof(int));
+constexpr size_t kOffsetsOff = kCountsOff + align256((kMaxBricks + 1) * sizeof(int));   // + ticket
 constexpr size_t kKeysOff = kOffsetsOff + align256((kMaxBricks + 1) * sizeof(int));
 constexpr size_t kSlotsOff = kKeysOff + align256(kMaxPositions * sizeof(int));
 constexpr size_t kPermOff = kSlotsOff + align256(kMaxPositions * sizeof(int));
