@@ -131,8 +131,7 @@ def test_ragged_reduced_precision(spo_lib, oracle_lib, storage, N):
 def test_f16_special_values(spo_lib, oracle_lib, kind):
     """FP16 tables holding zeros of both signs, subnormals, the smallest and
     largest normals and values that round into the subnormal range, mixed
-    with ordinary ones: the kernels widen every stored half exactly (normal
-    halves by integer operations, the rest by the library conversion)."""
+    with ordinary ones: every strategy widens each stored half exactly."""
     rng = np.random.default_rng(23)
     special = np.array([0.0, -0.0, 2.0 ** -24, -(2.0 ** -24), 3 * 2.0 ** -24, 2.0 ** -15,
                         2.0 ** -14, -(2.0 ** -14), 2.0 ** -14 - 2.0 ** -24, 65504.0, -65504.0,
@@ -416,3 +415,28 @@ def test_autotune_picks_a_strategy_and_keeps_outputs(spo_lib, tmp_path, monkeypa
         again = s.autotune("vgl", 7000)                # same power-of-two bucket
         assert again["from_cache"] and again["algo"] == best["algo"]
     assert cache.exists() and "kind=1" in cache.read_text()
+
+
+@pytest.mark.parametrize("kind", ["vgh", "v"])
+def test_reserved_evaluation_replays_in_a_cuda_graph(spo_lib, kind):
+    """After spo_reserve on a stream, an evaluation on that stream (binning
+    and brick kernel) can be captured in a CUDA graph; each replay evaluates
+    the positions the buffer holds then, bit for bit as a direct call."""
+    import torch as t
+    c = inputs.plane_wave_coefs(16, 12, 20, 64, seed=19).astype(np.float32)
+    P = 6000
+    with spo_lib.OrbitalSet(c) as s:
+        stream = t.cuda.Stream()
+        pos = t.from_numpy(inputs.uniform_positions(P, 31)).cuda()
+        out = t.empty(s.out_shape(P, kind), device="cuda")
+        s.reserve(P, stream=stream)
+        t.cuda.synchronize()
+        g = t.cuda.CUDAGraph()
+        with t.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+            s.eval(pos, kind, out=out, algo="brick")
+        for step in range(2):
+            pos.copy_(t.from_numpy(inputs.uniform_positions(P, 40 + step)))
+            g.replay()
+            t.cuda.synchronize()
+            assert spo_lib.device_status() == 0
+            assert t.equal(out, s.eval(pos, kind, algo="brick"))
