@@ -75,12 +75,9 @@ cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const S
 constexpr int kImgRows = 128, kImgK = 64;
 constexpr uint32_t kImgTileBytes = kImgRows * kImgK * 2;
 size_t bf16_image_bytes(int64_t rows, int64_t K);
-// src: FP32 [R][C] row major, leading dimension ld.  transpose = false: the
-// image of src (rows R, K = C); true: the image of src^T (rows C, K = R).
-cudaError_t to_bf16_image(const float *src, int64_t R, int64_t C, int64_t ld, bool transpose, uint8_t *img,
-                          cudaStream_t stream);
-// Both images of the R x C matrix in one pass: img_direct as
-// to_bf16_image(..., false, ...) and img_transposed as (..., true, ...).
+// Both images of src, FP32 [R][C] row major with leading dimension ld, in
+// one pass: img_direct the image of src (rows R, K = C), img_transposed the
+// image of src^T (rows C, K = R).
 cudaError_t to_bf16_images(const float *src, int64_t R, int64_t C, int64_t ld, uint8_t *img_direct,
                            uint8_t *img_transposed, cudaStream_t stream);
 // C[M][N] (row major, ld N) = A B^T from the images of A [M][K] and B [N][K];

@@ -7,8 +7,8 @@
 // byte ((mt * KB + kb) * 16384), each tile in the 128-byte swizzle layout
 // of a K-major MMA operand (row r at r * 128 bytes, its 16-byte chunks
 // permuted by r mod 8); rows beyond M and columns beyond K are zero, so the
-// MMAs may always run on whole tiles.  to_bf16_image writes such images from
-// an FP32 row-major matrix or from its transpose.
+// MMAs may always run on whole tiles.  to_bf16_images writes both images of
+// an FP32 row-major matrix (of it and of its transpose) in one pass.
 //
 // GEMM: one CTA (128 threads) per 128 x 128 output tile and K range.  One
 // thread streams (A, B) tile pairs with bulk copies through 3 shared-memory
@@ -41,45 +41,6 @@ constexpr uint32_t smem_bytes(int stages) { return (uint32_t)stages * kStageByte
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-// One thread per 16-byte chunk (8 BF16 of one image row).  Non-transposed:
-// image row = source row, K = source column (consecutive threads take
-// consecutive chunks of a row); transposed: image row = source column,
-// K = source row (consecutive threads take consecutive image rows, so the
-// reads of one source row are coalesced).
-__global__ void to_image_kernel(const float *__restrict__ src, int64_t R, int64_t C, int64_t ld,
-                                int transpose, int64_t rows_pad, int64_t kc_n, uint8_t *__restrict__ img) {
-    const int64_t total = rows_pad * kc_n;
-    const int64_t KB = kc_n / 8;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t row, kc;
-        if (transpose) {
-            kc = e / rows_pad;
-            row = e - kc * rows_pad;
-        } else {
-            row = e / kc_n;
-            kc = e - row * kc_n;
-        }
-        const int64_t k0 = kc * 8;
-        float v[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int64_t k = k0 + j;
-            float x = 0.0f;
-            if (transpose) {
-                if (k < R && row < C) x = __ldg(src + k * ld + row);
-            } else {
-                if (row < R && k < C) x = __ldg(src + row * ld + k);
-            }
-            v[j] = x;
-        }
-        const int64_t mt = row / kRowsT, kb = kc / 8;
-        uint8_t *tile = img + (size_t)(mt * KB + kb) * kTileBytes;
-        *reinterpret_cast<uint4 *>(tile + sw128_offset((int)(row % kRowsT), (int)(kc % 8) * 8)) =
-            make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
-    }
 }
 
 // Both images of an FP32 row-major R x C matrix in one pass: img_d with
@@ -272,18 +233,6 @@ namespace spo_detail {
 size_t bf16_image_bytes(int64_t rows, int64_t K) {
     const int64_t rp = (rows + kRowsT - 1) / kRowsT, kb = (K + kColsT - 1) / kColsT;
     return (size_t)rp * (size_t)kb * kTileBytes;
-}
-
-cudaError_t to_bf16_image(const float *src, int64_t R, int64_t C, int64_t ld, bool transpose, uint8_t *img,
-                          cudaStream_t stream) {
-    const int64_t rows = transpose ? C : R, K = transpose ? R : C;
-    const int64_t rows_pad = (rows + kRowsT - 1) / kRowsT * kRowsT;
-    const int64_t kc_n = (K + kColsT - 1) / kColsT * 8;
-    const int64_t total = rows_pad * kc_n;
-    if (total == 0) return cudaSuccess;
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
-    to_image_kernel<<<blocks, 256, 0, stream>>>(src, R, C, ld, transpose ? 1 : 0, rows_pad, kc_n, img);
-    return cudaGetLastError();
 }
 
 cudaError_t to_bf16_images(const float *src, int64_t R, int64_t C, int64_t ld, uint8_t *img_direct,
