@@ -87,20 +87,9 @@ def kernel_source_digest() -> str:
 
 
 def resolve_algo(name: str, s, P: int, kind: str) -> str:
-    """The strategy "auto" picks for this set and batch (mirrors the library's
-    rule, so that the launch count and the timed kernel are known)."""
-    if name != "auto":
-        return name
-    g = s.grid
-    nbins = 1
-    for n in g:
-        nbins *= (n + 3) // 4
-    if P < 1024 or 2 * P < 3 * nbins:
-        return "gather"
-    brick_from = {"vgh": 3, "vgl": 8, "v": 12}[kind]
-    if s.info()["Np"] >= 32 and P >= brick_from * nbins:
-        return "brick"
-    return "sorted_gather"
+    """The strategy a call with algo=name takes (the library's answer for
+    "auto"), so that the launch count and the timed kernel are known."""
+    return s.auto_algo(kind, P) if name == "auto" else name
 
 
 def recorded_traffic(workload: str, storage: str, kind: str, tuning: str):

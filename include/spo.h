@@ -173,6 +173,14 @@ spo_status spo_eval_ex(const spo_set *set, spo_kind kind, const float *pos, int6
                        float *out, void *stream, spo_algo algo);
 
 /*
+ * spo_auto_algo — the strategy SPO_ALGO_AUTO takes for this set, kind and
+ * batch size P (the rule above, or the tuned choice), written to *algo:
+ * SPO_ALGO_GATHER, SPO_ALGO_SORTED_GATHER or SPO_ALGO_BRICK.  Host only;
+ * SPO_EINVAL for a NULL argument, an unknown kind or P < 0.
+ */
+spo_status spo_auto_algo(const spo_set *set, spo_kind kind, int64_t P, spo_algo *algo);
+
+/*
  * spo_eval_ratio — determinant ratios of proposed moves, fused with the
  * value evaluation (Sec. 3, Alg. 1 "ratio", eq. md_lemma: moving electron k
  * to r' gives det(A')/det(A) = row k of A^-1 dotted with (phi_1(r'), ...,

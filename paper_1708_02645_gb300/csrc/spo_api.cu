@@ -199,16 +199,19 @@ spo_status check_binned_algo(const spo_set *set, spo_algo algo) {
     return SPO_OK;
 }
 
+// The strategy AUTO resolves to: the tuned choice for batches within 4x of
+// the tuned size, else choose_algo.
+spo_algo resolve_auto(const spo_set *set, spo_kind kind, int64_t P) {
+    const int k = (int)kind;
+    const int64_t tp = set->tuned_P[k];
+    return (set->tuned_algo[k] != 0 && P * 4 >= tp && P <= tp * 4) ? static_cast<spo_algo>(set->tuned_algo[k])
+                                                                     : choose_algo(set, kind, P);
+}
+
 // Queue one evaluation (arguments already checked; device already current).
 spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
                       cudaStream_t stream, spo_algo algo) {
-    if (algo == SPO_ALGO_AUTO) {
-        const int k = (int)kind;
-        const int64_t tp = set->tuned_P[k];
-        algo = (set->tuned_algo[k] != 0 && P * 4 >= tp && P <= tp * 4)
-                   ? static_cast<spo_algo>(set->tuned_algo[k])
-                   : choose_algo(set, kind, P);
-    }
+    if (algo == SPO_ALGO_AUTO) algo = resolve_auto(set, kind, P);
     if (algo == SPO_ALGO_GATHER) {
         cudaError_t e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
                                                   nullptr, P, out, stream);
@@ -691,6 +694,16 @@ spo_status spo_get_param(const spo_set *set, spo_param param, int64_t *value) {
         case SPO_PARAM_BRICK_SCHEDULE: *value = set->brick_schedule; return SPO_OK;
     }
     return fail(SPO_EINVAL, "unknown parameter %d", (int)param);
+}
+
+spo_status spo_auto_algo(const spo_set *set, spo_kind kind, int64_t P, spo_algo *algo) {
+    g_last_error[0] = '\0';
+    if (!set || !algo) return fail(SPO_EINVAL, "set or algo is NULL");
+    if (kind != SPO_KIND_V && kind != SPO_KIND_VGL && kind != SPO_KIND_VGH)
+        return fail(SPO_EINVAL, "unknown kind %d", (int)kind);
+    if (P < 0) return fail(SPO_EINVAL, "P = %lld is negative", (long long)P);
+    *algo = resolve_auto(set, kind, P);
+    return SPO_OK;
 }
 
 spo_status spo_footprint(const spo_set *set, size_t *bytes) {

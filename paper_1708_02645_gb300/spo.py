@@ -55,6 +55,7 @@ SIGNATURES = [
     ("spo_eval_host", _INT, [_P, _INT, _P, _I64, _P, _P]),
     ("spo_set_param", _INT, [_P, _INT, _I64]),
     ("spo_get_param", _INT, [_P, _INT, ctypes.POINTER(_I64)]),
+    ("spo_auto_algo", _INT, [_P, _INT, _I64, ctypes.POINTER(_INT)]),
     ("spo_footprint", _INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     ("spo_info", _INT, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_INT)]),
     ("spo_selftest_wait", _INT, [ctypes.c_uint64, _P, ctypes.POINTER(_INT)]),
@@ -235,6 +236,13 @@ class OrbitalSet:
         b = ctypes.c_size_t()
         _check(load().spo_footprint(self.handle, ctypes.byref(b)), "spo_footprint")
         return int(b.value)
+
+    def auto_algo(self, kind, P: int) -> str:
+        """The strategy algo="auto" takes for this kind and batch size."""
+        k = KINDS[kind] if isinstance(kind, str) else int(kind)
+        a = _INT()
+        _check(load().spo_auto_algo(self.handle, k, int(P), ctypes.byref(a)), "spo_auto_algo")
+        return {v: n for n, v in ALGOS.items()}[a.value]
 
     def info(self):
         g = _Grid()

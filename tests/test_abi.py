@@ -77,6 +77,8 @@ def test_eval_rejects_bad_arguments_before_cuda(lib):
     assert lib.spo_eval_host(None, 2, fake, 1, fake, None) == 1
     b = ctypes.c_size_t()
     assert lib.spo_footprint(None, ctypes.byref(b)) == 1
+    a = ctypes.c_int(-1)
+    assert lib.spo_auto_algo(None, 2, 100, ctypes.byref(a)) == 1 and a.value == -1
     assert lib.spo_destroy(None) == 0
 
 

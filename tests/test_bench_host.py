@@ -48,28 +48,6 @@ def test_smem_peak_is_derived_from_bank_count_and_clock():
     assert "banks" in src
 
 
-class _FakeSet:
-    def __init__(self, grid, Np):
-        self.grid, self._Np = grid, Np
-
-    def info(self):
-        return {"Np": self._Np}
-
-
-def test_auto_strategy_follows_positions_per_brick():
-    s = _FakeSet((64, 64, 64), 384)          # 16^3 = 4096 bricks
-    assert bench.resolve_algo("auto", s, 1000, "vgh") == "gather"
-    assert bench.resolve_algo("auto", s, 4096, "v") == "gather"          # r = 1
-    assert bench.resolve_algo("auto", s, 8192, "vgh") == "sorted_gather"  # r = 2
-    assert bench.resolve_algo("auto", s, 12288, "vgh") == "brick"        # r = 3
-    assert bench.resolve_algo("auto", s, 16384, "vgl") == "sorted_gather"
-    assert bench.resolve_algo("auto", s, 32768, "vgl") == "brick"        # r = 8
-    assert bench.resolve_algo("auto", s, 32768, "v") == "sorted_gather"
-    assert bench.resolve_algo("auto", s, 98304, "v") == "brick"          # r = 24
-    assert bench.resolve_algo("auto", _FakeSet((64, 64, 64), 16), 98304, "vgh") == "sorted_gather"
-    assert bench.resolve_algo("brick", s, 10, "v") == "brick"
-
-
 def test_fp32_peak_is_derived_from_unit_counts_and_clock():
     tf, src = bench.fp32_peak_tflops(152)
     assert abs(tf - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-6 or "MEASURED" in src

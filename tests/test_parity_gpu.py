@@ -440,3 +440,23 @@ def test_reserved_evaluation_replays_in_a_cuda_graph(spo_lib, kind):
             t.cuda.synchronize()
             assert spo_lib.device_status() == 0
             assert t.equal(out, s.eval(pos, kind, algo="brick"))
+
+
+def test_auto_strategy_follows_positions_per_brick(spo_lib):
+    """spo_auto_algo: gather below 1.5 positions per brick (or P < 1024),
+    the brick kernel from 3 (VGH), 8 (VGL) or 12 (V) per brick, the gather in
+    binned order between; sets with fewer than 32 padded orbitals never take
+    the brick kernel."""
+    c = inputs.uniform_coefs(64, 64, 64, 40, seed=5).astype(np.float32)   # 16^3 = 4096 bricks
+    with spo_lib.OrbitalSet(c) as s:
+        expect = [(1000, "vgh", "gather"), (4096, "v", "gather"), (8192, "vgh", "sorted_gather"),
+                  (12288, "vgh", "brick"), (16384, "vgl", "sorted_gather"), (32768, "vgl", "brick"),
+                  (32768, "v", "sorted_gather"), (49152, "v", "brick"), (98304, "v", "brick")]
+        for P, kind, algo in expect:
+            assert s.auto_algo(kind, P) == algo, (P, kind)
+        with pytest.raises(Exception):
+            s.auto_algo("vgh", -1)
+    small = inputs.uniform_coefs(64, 64, 64, 8, seed=6).astype(np.float32)
+    with spo_lib.OrbitalSet(small) as s:
+        assert s.auto_algo("vgh", 98304) == "sorted_gather"
+
