@@ -7,9 +7,9 @@
  * position, the values phi_i(r) of all orbitals ("ratio", through the
  * determinant lemma, eq. md_lemma) and their gradients and Laplacians
  * ("derivatives").  Sec. 6.1 names the B-spline routines Bspline-v,
- * Bspline-vgh and SPO-vgl; Sec. 6.2 describes their data as a
- * "4-dimensional read-only table" shared by all threads, read at random and
- * bound by memory bandwidth; Sec. 5.2 keeps that table and its evaluation in
+ * Bspline-vgh and SPO-vgl; by Sec. 6.2 their data is a read-only table with
+ * four indices (three grid axes and the orbital), shared by all threads,
+ * read at random and bound by memory bandwidth; Sec. 5.2 keeps that table and its evaluation in
  * single precision.  The B-spline itself is cited, not printed, in Sec. 3;
  * this library uses the uniform cubic B-spline on the periodic unit cube:
  *
