@@ -9,8 +9,8 @@
  * What it computes (arXiv 1708.02645, Sec. 3 "QMC algorithms": the Slater
  * matrix entries A(i,j) = phi_i(r_j) and their derivatives needed by Alg. 1
  * "ratio" and "derivatives"; Sec. 6.1 names the routines Bspline-v,
- * Bspline-vgh and SPO-vgl; the table is the "4-dimensional read-only table"
- * of Sec. 6.2).  The paper cites but does not print the B-spline formula;
+ * Bspline-vgh and SPO-vgl; the table is Sec. 6.2's read-only table with
+ * four indices).  The paper cites but does not print the B-spline formula;
  * this file follows the textbook uniform cubic B-spline:
  *
  *   B3(s) = (2-|s|)^3/6              1 <= |s| < 2
