@@ -58,7 +58,7 @@ typedef enum {
     SPO_ENOMEM = 2,        /* device or host allocation failed */
     SPO_ECUDA = 3,         /* a CUDA runtime call or launch failed */
     SPO_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
-    SPO_EUNSUPPORTED = 5   /* valid request this build does not implement */
+    SPO_EUNSUPPORTED = 5   /* a valid request the library does not support */
 } spo_status;
 
 typedef enum {
