@@ -1,9 +1,33 @@
-"""The seeded input recipes that are more than a random draw: the NLPP
-quadrature batch (icosahedron rule, rotations, points on the spheres about
-the ions)."""
+"""The seeded input recipes: the counter-based generator against its
+published outputs, and the recipes that are more than a random draw (the
+NLPP quadrature batch: icosahedron rule, rotations, points on the spheres
+about the ions)."""
 import numpy as np
 
 from paper_1708_02645_gb300 import inputs
+
+
+def test_splitmix64_matches_the_published_sequence():
+    # SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) from state 0: the
+    # well-known first outputs of the reference implementation
+    assert [int(x) for x in inputs.splitmix64(0, 4)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    # counter based: a stream drawn from an offset is the tail of the full one
+    full = inputs.splitmix64(12345, 64)
+    assert np.array_equal(inputs.splitmix64(12345, 40, offset=24), full[24:])
+
+
+def test_uniform_and_normal_streams():
+    u = inputs.uniform01(7, 200000)
+    assert u.min() >= 0.0 and u.max() < 1.0
+    assert abs(u.mean() - 0.5) < 5e-3 and abs(u.var() - 1.0 / 12.0) < 5e-3
+    z = inputs.normal(8, 200001)
+    assert len(z) == 200001
+    assert abs(z.mean()) < 1e-2 and abs(z.var() - 1.0) < 1e-2
+    p = inputs.uniform_positions(1000, 9)
+    assert p.dtype == np.float32 and p.min() >= 0.0 and p.max() < 1.0
+    # multiples of 2^-24: exact in FP32
+    assert np.array_equal(p.astype(np.float64) * 2.0 ** 24, np.round(p.astype(np.float64) * 2.0 ** 24))
 
 
 def test_icosahedron_rule_integrates_low_degree_harmonics():
