@@ -111,3 +111,37 @@ def test_reference_arm_prints_one_line(monkeypatch, capsys):
     d = json.loads(line)
     assert d["impl"] == "reference" and d["unit"] == "evals/s" and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_compulsory_bytes_are_table_positions_and_outputs():
+    assert bench.compulsory_bytes(10, 3, "f32", "vgh", 1000) == 1000 + 12 * 10 + 4 * 10 * 10 * 3
+    assert bench.compulsory_bytes(10, 3, "bf16", "v", 500) == 500 + 12 * 10 + 4 * 1 * 10 * 3
+
+
+def test_hbm_peak_is_measured_else_fallback(monkeypatch, tmp_path):
+    gbs, src = bench.measured_hbm_peak()
+    assert gbs > 0 and src in ("measured", "fallback")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))   # no MEASURED_PEAKS.json there
+    assert bench.measured_hbm_peak() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 1234.5}))
+    assert bench.measured_hbm_peak() == (1234.5, "measured")
+
+
+def test_oracle_timing_is_bounded_and_counts_evaluations():
+    import numpy as np
+    from paper_1708_02645_gb300 import inputs
+    c = inputs.uniform_coefs(8, 8, 8, 16, seed=3)
+    pos = inputs.uniform_positions(300, 4)
+    rate, n, reps, cores, dt = bench.oracle_throughput(c, pos, "vgh", 0.05)
+    assert 0 < n <= len(pos) and reps >= 1 and cores >= 1 and dt > 0
+    assert abs(rate - reps * n * 16 / dt) <= 1e-6 * rate
+    rate1, n1, dt1 = bench.oracle_single_thread(c, pos, "v", 0.05)
+    assert rate1 > 0 and 0 < n1 <= len(pos) and dt1 > 0
+
+
+def test_workload_config_names_the_bench_shapes():
+    from paper_1708_02645_gb300 import inputs
+    cfg = bench.workload_config(inputs.NIO64.name)
+    assert cfg.grid == (64, 64, 64) and cfg.N == 384 and cfg.P == 98304
+    c = bench.base_config(cfg, "f32", "vgh", cfg.P)
+    assert c["workload"] == "nio64_64cubed_n384" and c["positions"] == 98304 and c["orbitals"] == 384
