@@ -313,7 +313,9 @@ def measure_e2e(args, s, pos_np, out, kind, evals_per_step, world, dev):
     return e2e
 
 
-FLOPS_PER_EVAL = {"v": 168, "vgl": 600, "vgh": 656}   # factored z -> y -> x sums, FMA = 2
+# 2 x the FMA-pipe operations of the factored z -> y -> x sums per evaluation
+# (each sum's first term is a multiply, which the FMA pipe takes like an FMA)
+FLOPS_PER_EVAL = {"v": 168, "vgl": 600, "vgh": 656}
 FP32_LANES_PER_SM = 128
 
 
@@ -463,6 +465,9 @@ def run_ours(args):
         "bound": "alu", "achieved": round(achieved_tf, 3), "peak": round(tf_peak, 2),
         "unit": "TFLOP/s", "frac": round(achieved_tf / tf_peak, 4),
         "peak_source": tf_src + "; FP32 FMA issue is what limits this kernel (ncu)",
+        "flop_note": "2 per FMA-pipe operation of the factored sums (a sum's first term is a multiply, "
+                     "which occupies the FMA pipe as an FMA): frac is the share of FMA-pipe slots "
+                     "doing algorithmic work",
         "traffic": recorded_traffic(cfg.name, storage, kind, tuning),
         "kernel": f"{kernel_name}<{storage},{kind}>", "kernel_ms": round(kernel_ms, 5),
         "flops_per_launch": flops, "flops_per_eval": FLOPS_PER_EVAL[kind],
