@@ -233,12 +233,18 @@ spo_status spo_eval_binned(const spo_set *set, spo_kind kind, const float *pos, 
  * and a grid of at most SPO_NOALLOC_MAX_BRICKS bricks of 4x4x4 cells; larger
  * requests return SPO_EINVAL without launching anything.
  *
+ * It takes the strategy spo_eval's SPO_ALGO_AUTO takes for the same set,
+ * kind and P, so its outputs equal spo_eval's bit for bit.
+ *
  * The first call on a device looks up the array's device address (once per
- * device, with the set's device current); make that first call before any
- * stream capture.  All calls on a device share the one array and it keeps
- * the last call's contents (each call clears what must start at zero):
- * calls whose GPU work overlaps, on different streams or from several host
- * threads, race and give wrong results, so order them (one stream does).
+ * device, with the set's device current, kept until the process exits:
+ * after cudaDeviceReset do not call it again); make that first call before
+ * any stream capture.  All calls on a device share the one array and it
+ * keeps the last call's contents; each call first clears, on its stream,
+ * what must start at zero (the brick counts).  Calls whose GPU work
+ * overlaps, on different streams or from several host threads, race: they
+ * give wrong results and may write outside their `out`, so order them (one
+ * stream does).
  */
 #define SPO_NOALLOC_MAX_POSITIONS 262144
 #define SPO_NOALLOC_MAX_BRICKS 65536

@@ -248,6 +248,8 @@ spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64
     return ::eval_queue(set, kind, pos, P, out, stream, algo);
 }
 
+spo_algo auto_algo(const spo_set *set, spo_kind kind, int64_t P) { return resolve_auto(set, kind, P); }
+
 spo_status fail(spo_status status, const char *fmt, ...) {
     va_list ap;
     va_start(ap, fmt);

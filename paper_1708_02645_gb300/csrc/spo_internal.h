@@ -87,6 +87,10 @@ spo_status fail(spo_status status, const char *fmt, ...);
 spo_status eval_queue(const spo_set *set, spo_kind kind, const float *pos, int64_t P, float *out,
                       cudaStream_t stream, spo_algo algo);
 
+// The strategy SPO_ALGO_AUTO resolves to for this set, kind and batch size
+// (the autotuned choice near the tuned size, else the measured rule).
+spo_algo auto_algo(const spo_set *set, spo_kind kind, int64_t P);
+
 // Geometry of one table as the kernels see it.
 struct TableView {
     const void *table;

@@ -16,11 +16,22 @@
 // SPO_NOALLOC_MAX_BRICKS bricks of 4x4x4 cells in the set's grid.
 //
 // The array is shared by every call on a device and keeps the contents of
-// the last call: the brick counts are cleared (a memset) at the start of
-// each call, everything else is overwritten before it is read.  Calls whose
-// work overlaps on the GPU (on different streams, or from several host
-// threads) race on the array and give wrong results; order them, for
+// the last call.  Each call first clears the brick counts and the binning's
+// ticket (a cudaMemsetAsync on the call's stream, which allocates nothing);
+// everything else is overwritten before it is read.  Calls whose work
+// overlaps on the GPU (on different streams, or from several host threads)
+// race on the array and give wrong results, and may write outside `out`
+// (a count raised by the other call moves this call's sorted slots past P);
+// the clear confines the damage to the overlapping calls.  Order them, for
 // example on one stream.
+//
+// The strategy is the one spo_eval's AUTO takes for the same set, kind and
+// batch size (the gather kernel, in input order or in binned order, or the
+// brick kernel), so the outputs are those of spo_eval bit for bit.
+//
+// The array's device address is looked up once per device and kept for the
+// life of the process; after cudaDeviceReset the old address is stale and
+// this entry point must not be called again in that process.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -112,7 +123,14 @@ extern "C" spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const 
     if (st == SPO_OK) st = device_pointer(out, set->device, "out");
     unsigned char *base = nullptr;
     if (st == SPO_OK) st = scratch_address(set->device, &base);
-    if (st == SPO_OK) {
+    const spo_algo algo = spo_detail::auto_algo(set, kind, P);
+    if (st == SPO_OK && algo == SPO_ALGO_GATHER) {
+        // input order: no binning, the scratch is not touched
+        cudaError_t e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
+                                                  nullptr, P, out, static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess)
+            st = fail(SPO_ECUDA, "spo_eval_noalloc launch: %s", cudaGetErrorString(e));
+    } else if (st == SPO_OK) {
         spo_detail::Workspace w;
         w.stream = static_cast<cudaStream_t>(stream);
         w.counts = reinterpret_cast<int *>(base + kCountsOff);
@@ -123,10 +141,13 @@ extern "C" spo_status spo_eval_noalloc(const spo_set *set, spo_kind kind, const 
         w.sorted = reinterpret_cast<float4 *>(base + kSortedOff);
         w.cap_positions = (int64_t)kMaxPositions;
         w.cap_bins = (int64_t)kMaxBricks;
-        cudaError_t e = spo_detail::launch_bin(pos, P, set->nx, set->ny, set->nz, set->nbx, set->nby,
-                                               set->nbz, w, w.stream);
+        // the binning needs counts[0..bricks) and the ticket counts[bricks] at zero
+        cudaError_t e = cudaMemsetAsync(w.counts, 0, (size_t)(bricks + 1) * sizeof(int), w.stream);
+        if (e == cudaSuccess)
+            e = spo_detail::launch_bin(pos, P, set->nx, set->ny, set->nz, set->nbx, set->nby,
+                                       set->nbz, w, w.stream);
         if (e == cudaSuccess) {
-            if (set->has_block_map)
+            if (algo == SPO_ALGO_BRICK)
                 e = spo_detail::launch_brick(set->storage, kind, set, pos, w, P, out, w.stream);
             else
                 e = spo_detail::launch_gather(set->storage, kind, spo_detail::view_of(set), pos,
