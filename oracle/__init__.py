@@ -12,7 +12,13 @@ plain 64-term window sum of weight products times coefficients (arXiv
 gradients and Laplacians needed by Alg. 1; Sec. 6.1 for the Bspline-v,
 Bspline-vgh and SPO-vgl routines; Sec. 6.2 for the read-only 4-D table).
 
-Parity status: pinned by ``tests/test_oracle_pins.py``.
+Parity status: pinned by ``tests/test_oracle_pins.py``: the evaluator by
+closed forms, brute force and invariants; the condition sums ``condition``
+and ``spo_ratio_condition`` (which set the per-element error bounds of the
+GPU tests) by their closed forms for tables with |c| constant, a brute-force
+sum of |B3 products| |c| over all images, beta_V = V for c >= 0 and
+beta_ratio = ratio for non-negative rows and c.  ``tests/test_oracle_mutants.py``
+plants slips in both and requires a pin to fail for each.
 """
 from __future__ import annotations
 

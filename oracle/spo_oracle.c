@@ -43,7 +43,9 @@
  * Parity status: pinned (see tests/test_oracle_pins.py: partition of unity,
  * impulse response, polynomial reproduction, plane-wave closed form at
  * nodes, C2 continuity, finite differences, periodic wrap, brute-force
- * global sum, linearity).
+ * global sum, linearity); the condition sums by their closed forms for
+ * tables with constant |c|, a brute-force sum over all images, and
+ * beta_V = V for non-negative tables.
  */
 #include <math.h>
 #include <stddef.h>

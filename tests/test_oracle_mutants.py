@@ -30,7 +30,57 @@ MUTANTS = {
     "fraction_sign": ("double t = u - fl;", "double t = fl - u + 1.0;"),
     "ny_for_nz": ("basis_weights(tz, nz, wz, dwz, d2wz);\n\n    for (long k",
                   "basis_weights(tz, ny, wz, dwz, d2wz);\n\n    for (long k"),
+    # slips in the condition sums (oracle_spo_condition), which set every
+    # per-element bound of the GPU parity tests
+    "cond_dropped_abs_c": ("hq[j] += aw * fabs(c[j]);", "hq[j] += aw * c[j];"),
+    "cond_dropped_abs_w": ("double aw = fabs(W[q]);", "double aw = W[q];"),
+    "cond_weights_only": ("hq[j] += aw * fabs(c[j]);", "hq[j] += aw;"),
+    "cond_wrong_component": ("                    W[6] = dwx[a] * wy[b] * dwz[g];",
+                             "                    W[6] = dwx[a] * dwy[b] * wz[g];"),
+    "cond_stray_factor_n": ("double aw = fabs(W[q]);", "double aw = fabs(W[q]) * nx;"),
+    "cond_window_offset": ("            long xa = (ix + a - 1 + nx) % nx;",
+                           "            long xa = (ix + a + nx) % nx;"),
 }
+
+# slips in the Python side of the oracle (oracle/__init__.py)
+PY_MUTANTS = {
+    "laplacian_beta_rows": ("(b[:, 4] + b[:, 7] + b[:, 9])", "(b[:, 4] + b[:, 5] + b[:, 9])"),
+    "laplacian_beta_whole_hessian": ("(b[:, 4] + b[:, 7] + b[:, 9])", "b[:, 4:10].sum(axis=1)"),
+    "ratio_condition_signed_rows": ("rows = np.abs(np.asarray(rows, dtype=np.float64))",
+                                    "rows = np.asarray(rows, dtype=np.float64)"),
+    "ratio_condition_ignores_row_of": (
+        "rows = np.abs(np.asarray(rows, dtype=np.float64))\n"
+        "    idx = np.arange(b.shape[0]) if row_of is None else np.asarray(row_of)",
+        "rows = np.abs(np.asarray(rows, dtype=np.float64))\n    idx = np.arange(b.shape[0])"),
+}
+
+
+def oracle_variant(py_source, lib):
+    """A copy of the oracle package's module, executed from `py_source` and
+    bound to the compiled library `lib`."""
+    import types
+
+    import oracle
+    mod = types.ModuleType("oracle_variant")
+    mod.__file__ = oracle.__file__
+    exec(compile(py_source, oracle.__file__, "exec"), mod.__dict__)
+    mod._lib = lib
+    return mod
+
+
+def failed_pins(o):
+    """names of the pins (evaluator and condition checks) the module o fails"""
+    def ev(coefs, pos, kind=pins.KIND_VGH):
+        return o.spo_eval(coefs, pos, kind)
+
+    caught = []
+    for check, arg in [(c, ev) for c in pins.ALL_CHECKS] + [(c, o) for c in pins.CONDITION_CHECKS]:
+        try:
+            with np.errstate(all="ignore"):
+                check(arg)
+        except (AssertionError, IndexError, ValueError):   # wrong values, or unusable output
+            caught.append(check.__name__)
+    return caught
 
 
 @pytest.fixture(scope="module")
@@ -40,8 +90,15 @@ def oracle_source():
         return f.read()
 
 
+@pytest.fixture(scope="module")
+def oracle_py_source():
+    import oracle
+    with open(oracle.__file__) as f:
+        return f.read()
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(name, oracle_source, tmp_path, oracle_lib):
+def test_mutant_is_caught(name, oracle_source, oracle_py_source, tmp_path, oracle_lib):
     old, new = MUTANTS[name]
     assert oracle_source.count(old) >= 1, f"mutation site for {name} not found"
     src = oracle_source.replace(old, new, 1)
@@ -50,16 +107,18 @@ def test_mutant_is_caught(name, oracle_source, tmp_path, oracle_lib):
     so = tmp_path / f"lib{name}.so"
     subprocess.run(["gcc", "-O1", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                     "-o", str(so), str(cpath), "-lm"], check=True)
-    lib = oracle_lib.load_variant(str(so))
+    o = oracle_variant(oracle_py_source, oracle_lib.load_variant(str(so)))
+    assert failed_pins(o), f"mutant {name} passed every pin"
 
-    def ev(coefs, pos, kind=pins.KIND_VGH):
-        return pins.oracle_ev(coefs, pos, kind, lib=lib)
 
-    caught = []
-    for check in pins.ALL_CHECKS:
-        try:
-            with np.errstate(all="ignore"):
-                check(ev)
-        except AssertionError:
-            caught.append(check.__name__)
-    assert caught, f"mutant {name} passed every pin"
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_python_mutant_is_caught(name, oracle_py_source, oracle_lib):
+    old, new = PY_MUTANTS[name]
+    assert oracle_py_source.count(old) == 1, f"mutation site for {name} not found or ambiguous"
+    o = oracle_variant(oracle_py_source.replace(old, new), oracle_lib._load())
+    assert failed_pins(o), f"mutant {name} passed every pin"
+
+
+def test_unmutated_copies_pass(oracle_source, oracle_py_source, oracle_lib):
+    """the mutation machinery itself: an unchanged copy passes every pin"""
+    assert failed_pins(oracle_variant(oracle_py_source, oracle_lib._load())) == []

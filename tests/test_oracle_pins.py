@@ -306,6 +306,171 @@ def test_oracle_pin(oracle_lib, check):
     check(oracle_ev)
 
 
+# ---------------------------------------------------------------------------
+# condition sums beta_q = sum over the window of |W_q| |c| (the scale of the
+# rounding error of any evaluation of the same sums; they set the per-element
+# bounds of every GPU parity test).  Each check takes an oracle-like module
+# `o` (spo_eval, condition, spo_ratio, spo_ratio_condition), so that the
+# mutant tests can run them on broken copies.
+#
+# Closed forms, derived from the cubic B-spline pieces on one cell (t in
+# [0, 1], derivatives with respect to u = r n):
+#   sum_a |w_a|   = 1                        (w_a >= 0, partition of unity)
+#   sum_a |w'_a|  = 1 + 2 t (1 - t)          (w'_0, w'_1 <= 0 <= w'_2, w'_3 and
+#                                             sum w' = 0: twice the positive part,
+#                                             w'_2 + w'_3 = (1 + 2t - 2t^2)/2)
+#   sum_a |w''_a| = max(2, 4 - 6 t, 6 t - 2) (w''_0 = 1-t, w''_3 = t >= 0;
+#                                             w''_1 = 3t-2, w''_2 = 1-3t change
+#                                             sign at t = 2/3 and 1/3)
+# With |c| = kappa_j for every node, beta of a tensor-product weight is
+# kappa_j times the product of these one-axis sums (times n_d per derivative).
+# ---------------------------------------------------------------------------
+def _frac(pos, ns):
+    """t_d = u_d - floor(u_d), u_d = r_d n_d (exact for FP32 positions)"""
+    u = np.asarray(pos, dtype=np.float64).reshape(-1, 3) * np.asarray(ns, dtype=np.float64)
+    return u - np.floor(u)
+
+
+def _abs_sum_d1(t):
+    return 1.0 + 2.0 * t * (1.0 - t)
+
+
+def _abs_sum_d2(t):
+    return np.maximum(2.0, np.maximum(4.0 - 6.0 * t, 6.0 * t - 2.0))
+
+
+def brute_force_condition(coefs, pos):
+    """beta_q(r) = sum over m in Z^3 of |prod_d n_d^k_d B3^(k_d)(u_d - m_d)|
+    |c[m mod n]| for the ten VGH derivative orders, with the piecewise B3 and
+    every integer m within 3 cells of u (no window bookkeeping)."""
+    coefs = np.abs(np.asarray(coefs, dtype=np.float64))
+    ns = coefs.shape[:3]
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((pos.shape[0], 10, coefs.shape[3]))
+    for p, r in enumerate(pos):
+        ms, bs = [], []
+        for d in range(3):
+            u = r[d] * ns[d]
+            m = np.arange(math.floor(u) - 3, math.floor(u) + 4)
+            ms.append(np.mod(m, ns[d]))
+            bs.append([b3(u - m, k) * float(ns[d]) ** k for k in range(3)])
+        cw = coefs[np.ix_(ms[0], ms[1], ms[2])]          # |c| of every image in range
+        for q, (kx, ky, kz) in enumerate(ORDERS):
+            w = np.abs(np.einsum("i,j,k->ijk", bs[0][kx], bs[1][ky], bs[2][kz]))
+            out[p, q] = np.einsum("ijk,ijkn->n", w, cw)
+    return out
+
+
+def _signed_constant_table(ns, kappa, seed):
+    """|c| = kappa_j at every node, random signs"""
+    rng = np.random.default_rng(seed)
+    sign = rng.choice([-1.0, 1.0], size=tuple(ns) + (len(kappa),))
+    return sign * np.asarray(kappa, dtype=np.float64)
+
+
+def _condition_positions(ns, seed):
+    nodes = np.stack([np.arange(6) % n / n for n in ns], axis=1)   # t = 0 on every axis
+    thirds = np.array([[1 / 3, 2 / 3, 0.5]]) / np.asarray(ns)      # kinks of sum |w''|
+    return np.concatenate([inputs.uniform_positions(40, seed).astype(np.float64),
+                           inputs.wide_positions(40, seed + 1).astype(np.float64),
+                           nodes, thirds])
+
+
+def check_condition_closed_forms(o):
+    ns = np.array([5, 6, 7])
+    kappa = np.array([0.5, 1.5, 2.0])
+    c = _signed_constant_table(ns, kappa, 61)
+    pos = _condition_positions(ns, 62)
+    t = _frac(pos, ns)
+    s1 = _abs_sum_d1(t) * ns                 # [P, 3]: n_d sum |w'|
+    s2 = _abs_sum_d2(t) * ns * ns            # n_d^2 sum |w''|
+    one = np.ones_like(t)
+    per_axis = [one, s1, s2]
+    want = np.empty((pos.shape[0], 10, 3))
+    for q, (kx, ky, kz) in enumerate(ORDERS):
+        f = per_axis[kx][:, 0] * per_axis[ky][:, 1] * per_axis[kz][:, 2]
+        want[:, q] = f[:, None] * kappa
+    got = o.condition(c, pos, KIND_VGH)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max(), np.abs(got - want).max()
+    lap = (s2.sum(axis=1))[:, None] * kappa
+    g = o.condition(c, pos, KIND_VGL)
+    assert np.abs(g[:, :4] - want[:, :4]).max() <= 1e-13 * np.abs(want[:, :4]).max()
+    assert np.abs(g[:, 4] - lap).max() <= 1e-13 * np.abs(lap).max()
+    assert np.abs(o.condition(c, pos, KIND_V) - kappa).max() <= 1e-14
+    # at a node every first-derivative sum is n_d (1/2 + 0 + 1/2)
+    at_nodes = o.condition(c, pos[80:86], KIND_VGH)
+    for d in range(3):
+        assert np.abs(at_nodes[:, GX + d] - ns[d] * kappa).max() <= 1e-13 * ns[d]
+
+
+def check_condition_of_nonnegative_table_is_value(o):
+    """c >= 0: every |W_V c| = W_V c, so beta_V equals V itself."""
+    ns = (6, 5, 7)
+    c = inputs.uniform_coefs(*ns, 4, seed=63) + 1.0          # in [0, 2)
+    pos = _condition_positions(ns, 64)
+    v = o.spo_eval(c, pos, KIND_V)
+    b = o.condition(c, pos, KIND_V)
+    assert np.abs(b - v).max() <= 1e-14 * np.abs(v).max()
+    # and beta dominates |output| for any signs (triangle inequality)
+    c2 = inputs.uniform_coefs(*ns, 4, seed=65)
+    h = o.spo_eval(c2, pos, KIND_VGH)
+    bh = o.condition(c2, pos, KIND_VGH)
+    assert (np.abs(h) <= bh * (1 + 1e-13) + 1e-300).all()
+
+
+def check_condition_brute_force(o):
+    for ns, N, seed in (((4, 4, 4), 2, 66), ((5, 4, 7), 3, 67), ((7, 5, 4), 2, 68)):
+        c = inputs.uniform_coefs(*ns, N, seed=seed)
+        pos = _condition_positions(ns, seed + 100)
+        ref = brute_force_condition(c, pos)
+        got = o.condition(c, pos, KIND_VGH)
+        assert_close_groups(got, ref, 1e-13, f"condition brute force {ns}")
+
+
+def check_ratio_condition(o):
+    """beta of a ratio: sum_j |row_j| beta_V,j.  For rows >= 0 and c >= 0 it
+    is the ratio itself; for |c| = kappa_j it is sum_j |row_j| kappa_j."""
+    ns, N, R = (6, 7, 5), 4, 3
+    rng = np.random.default_rng(69)
+    pos = _condition_positions(ns, 70)
+    P = pos.shape[0]
+    row_of = rng.integers(0, R, size=P)
+    rows = rng.uniform(0.1, 1.0, size=(R, N))
+    c = inputs.uniform_coefs(*ns, N, seed=71) + 1.0
+    rho = o.spo_ratio(c, pos, rows, row_of=row_of)
+    beta = o.spo_ratio_condition(c, pos, rows, row_of=row_of)
+    assert np.abs(beta - rho).max() <= 1e-13 * np.abs(rho).max()
+    kappa = np.array([0.25, 1.0, 3.0, 0.5])
+    cs = _signed_constant_table(ns, kappa, 72)
+    srows = rows * rng.choice([-1.0, 1.0], size=rows.shape)
+    beta = o.spo_ratio_condition(cs, pos, srows, row_of=row_of)
+    want = np.abs(srows[row_of]) @ kappa
+    assert np.abs(beta - want).max() <= 1e-13 * want.max()
+    # row_of = None means row p for position p
+    beta = o.spo_ratio_condition(cs, pos[:R], srows)
+    assert np.abs(beta - np.abs(srows) @ kappa).max() <= 1e-13 * want.max()
+
+
+CONDITION_CHECKS = [check_condition_closed_forms, check_condition_of_nonnegative_table_is_value,
+                    check_condition_brute_force, check_ratio_condition]
+
+
+@pytest.mark.parametrize("check", CONDITION_CHECKS, ids=lambda f: f.__name__)
+def test_condition_pin(oracle_lib, check):
+    check(oracle_lib)
+
+
+def test_brute_force_condition_reproduces_closed_values(oracle_lib):
+    """The brute force itself: at a node with c = 1 everywhere, beta_V = 1,
+    beta_Gx = n (B3'(+-1) = -+1/2), beta_Hxx = 4 n^2 (|B3''| = 1, 2, 1)."""
+    c = np.ones((4, 5, 6, 1))
+    out = brute_force_condition(c, np.array([[0.25, 0.4, 0.5]]))
+    assert abs(out[0, V, 0] - 1.0) < 1e-15
+    assert abs(out[0, GX, 0] - 4.0) < 1e-14
+    assert abs(out[0, HXX, 0] - 4.0 * 16.0) < 1e-12
+    assert abs(out[0, HYZ, 0] - 5.0 * 6.0) < 1e-12
+
+
 def test_brute_force_is_independent_of_window(oracle_lib):
     """The brute force itself reproduces B3's closed values (impulse at node)."""
     c = np.zeros((4, 4, 4, 1))
