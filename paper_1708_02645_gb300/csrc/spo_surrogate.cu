@@ -2,10 +2,13 @@
 // + softplus perceptron, with value / gradient / Laplacian carried through
 // the network as five channels (the function is specified in include/spo.h).
 //
-// Training (FP32 master parameters, CUDA cores): each step samples uniform
-// positions, asks the spline (the teacher) for their VGL, runs the forward
-// pass with channels, the loss, the hand-derived backward (encode, GEMMs,
-// softplus jets) and one Adam step.  Inference (precision 1) uses an FP16
+// Training (FP32 master parameters): each step samples uniform positions,
+// asks the spline (the teacher) for their VGL, runs the forward pass with
+// channels, the loss, the hand-derived backward (encode, GEMMs, softplus
+// jets) and one Adam step.  The layers' products run by default on the
+// tcgen05 tensor cores with BF16 operands and FP32 accumulation
+// (spo_tc_gemm.cu); spo_surrogate_set_train_precision(0) runs them in FP32
+// on the CUDA cores instead.  Inference (precision 1) uses an FP16
 // grid and BF16 weights; its perceptron runs on the tcgen05 tensor cores
 // (spo_surrogate_mma.cu); precision 0 evaluates the FP32 master parameters.
 //
