@@ -274,6 +274,52 @@ def oracle_single_thread(coefs64, pos, kind: str, target_s: float):
     return n * N / dt, n, dt
 
 
+PRECISION_SAMPLE = 4096
+
+
+def cpu_baseline_leg(args, cfg, pos_np, kind: str):
+    """The FP64 oracle on the host cores.  Returns the cpu_baseline entry
+    (its throughput on a bounded sample, all threads and one thread) and its
+    FP64 outputs (VGH and VGL, from the FP64 coefficients) at a seeded sample
+    of PRECISION_SAMPLE of the workload's positions: the reference against
+    which each storage format's error is reported."""
+    import oracle
+    P = len(pos_np)
+    coefs64 = cfg.make_coefs(np.float64)
+    v, n, reps, cores, dt = oracle_throughput(coefs64, pos_np, kind, args.cpu_seconds)
+    v1, n1, dt1 = oracle_single_thread(coefs64, pos_np, kind, min(3.0, args.cpu_seconds))
+    baseline = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                "sample": f"{n} of the {P} positions x {cfg.N} orbitals, "
+                          f"{reps} pass(es) ({kind.upper()}, FP64 oracle, "
+                          f"{dt:.1f} s on {cores} threads)",
+                "single_thread": {"value": v1, "unit": "evals/s",
+                                  "sample": f"{n1} positions x {cfg.N} orbitals, "
+                                            f"{dt1:.1f} s on 1 thread"}}
+    idx = np.sort(np.random.default_rng(cfg.seed + 4096).choice(
+        P, size=min(P, PRECISION_SAMPLE), replace=False))
+    sp = pos_np[idx].astype(np.float64)
+    ref = {"vgh": oracle.spo_eval(coefs64, sp, oracle.KIND_VGH),
+           "vgl": oracle.spo_eval(coefs64, sp, oracle.KIND_VGL)}
+    return baseline, {"idx": idx, "ref": ref}
+
+
+def error_vs_reference(sv, pos_sample, ref):
+    """Max and RMS relative error per output group (V, G, H from VGH; L from
+    VGL) of the set sv at the sampled positions against FP64 values:
+    max|d| / max|ref| and ||d|| / ||ref|| over positions x orbitals x
+    components.  Every strategy gives the same bits, so these are the rows
+    of the full-size launch at those positions."""
+    out = {}
+    for kd, groups in (("vgh", {"V": (0, 1), "G": (1, 4), "H": (4, 10)}), ("vgl", {"L": (4, 5)})):
+        got = sv.eval(pos_sample, kd, algo="auto").cpu().numpy().astype(np.float64)
+        r = ref[kd]
+        for g, (lo, hi) in groups.items():
+            d, rr = got[:, lo:hi] - r[:, lo:hi], r[:, lo:hi]
+            out[g] = {"max_rel": float(np.abs(d).max() / np.abs(rr).max()),
+                      "rms_rel": float(np.linalg.norm(d) / np.linalg.norm(rr))}
+    return out
+
+
 # ---------------------------------------------------------------------------
 # arms
 # ---------------------------------------------------------------------------
@@ -515,20 +561,13 @@ def run_ours(args):
     if world > 1:
         result["config"]["parallelism"] = f"replicas x{world} (positions sharded per rank)"
 
-    if rank == 0 and world == 1 and not args.no_variants:
-        result["variants"] = measure_variants(args, cfg, coefs32, s, pos, out, kind, storage, algo)
-
+    oracle_sample = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        coefs64 = cfg.make_coefs(np.float64)
-        v, n, reps, cores, dt = oracle_throughput(coefs64, pos_np, kind, args.cpu_seconds)
-        v1, n1, dt1 = oracle_single_thread(coefs64, pos_np, kind, min(3.0, args.cpu_seconds))
-        result["cpu_baseline"] = {"value": v, "unit": "evals/s", "cores": cores, "kind": "oracle",
-                                  "sample": f"{n} of the {P} positions x {cfg.N} orbitals, "
-                                            f"{reps} pass(es) ({kind.upper()}, FP64 oracle, "
-                                            f"{dt:.1f} s on {cores} threads)",
-                                  "single_thread": {"value": v1, "unit": "evals/s",
-                                                    "sample": f"{n1} positions x {cfg.N} orbitals, "
-                                                              f"{dt1:.1f} s on 1 thread"}}
+        result["cpu_baseline"], oracle_sample = cpu_baseline_leg(args, cfg, pos_np, kind)
+
+    if rank == 0 and world == 1 and not args.no_variants:
+        result["variants"] = measure_variants(args, cfg, coefs32, s, pos, out, kind, storage, algo,
+                                              oracle_sample)
     s.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -541,10 +580,12 @@ VARIANTS = ("all", "storage", "ratio", "nlpp", "autotune", "crowd", "surrogate",
             "prefilter", "nio32")
 
 
-def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
+def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo, oracle_sample=None):
     """Reduced-precision storage on the same positions (throughput, table
-    bytes, and the GPU-side difference from the FP32-storage outputs), and
-    the NiO-32-shaped set (V, VGL, VGH)."""
+    bytes, the error of every storage format against the FP64 oracle on the
+    FP64 coefficients at a seeded sample of the positions, and the
+    difference from the FP32-storage outputs), and the NiO-32-shaped set
+    (V, VGL, VGH)."""
     import torch
     from paper_1708_02645_gb300 import spo
     res = {}
@@ -556,6 +597,13 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
 
     if storage == "f32" and want("storage"):
         ref = out32.clone()
+        psample = None
+        if oracle_sample is not None:
+            psample = pos[torch.from_numpy(oracle_sample["idx"]).to(pos.device)]
+            res["precision_sample"] = (f"{len(oracle_sample['idx'])} positions drawn without "
+                                       f"replacement (seed {cfg.seed + 4096}) from the {pos.shape[0]}; "
+                                       "reference: the FP64 oracle on the FP64 coefficients")
+            res["f32_error_vs_oracle"] = error_vs_reference(s32, psample, oracle_sample["ref"])
         for st in ("bf16", "f16"):
             with spo.OrbitalSet(coefs32, storage=st) as sv:
                 configure(sv, args)
@@ -568,6 +616,8 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo):
                            "ms_per_step": round(step_ms, 5), "kernel_ms": round(k_ms, 5),
                            "table_bytes": sv.footprint(),
                            "max_rel_diff_vs_f32_storage": max_rel_diff(o, ref, kind)}
+                if psample is not None:
+                    res[st]["error_vs_oracle"] = error_vs_reference(sv, psample, oracle_sample["ref"])
         res["f32_table_bytes"] = s32.footprint()
     if want("ratio"):
         res["ratio_fused_v"] = measure_ratio(cfg, s32, pos, steps)
