@@ -385,6 +385,11 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  * spo_surrogate_set_optimizer(s, beta1, beta2, eps, grid_lr_mult): Adam's
  *   moment decay rates and denominator guard (defaults 0.9, 0.99, 1e-15),
  *   and the grid's learning rate as a multiple of `lr` (default 1).
+ * spo_surrogate_set_level_lr(s, power): the grid's rate of level l is
+ *   further multiplied by (R_0 / R_l)^power (0 <= power <= 4; default 0:
+ *   every level at lr * grid_lr_mult).  A feature of level l moves the
+ *   Laplacian channel R_l^2 times as much as the value channel, so with
+ *   power 2 every level's step changes the Laplacian alike.
  * spo_surrogate_nparams(s, &n) / spo_surrogate_state(s, params, m, v, &step,
  *   restore): the training state for checkpoints: all FP32 master parameters
  *   laid out [grid | W0 | b0 | W1 | b1 | ...] (n floats), Adam's first and
@@ -417,6 +422,7 @@ spo_status spo_surrogate_grad(spo_surrogate *s, const float *pos, const float *t
                               const float *channel_weights, int precision, float *loss, float *grid,
                               float *const *W, float *const *b, void *stream);
 spo_status spo_surrogate_set_train_precision(spo_surrogate *s, int precision);
+spo_status spo_surrogate_set_level_lr(spo_surrogate *s, float power);
 spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta2, float eps,
                                        float grid_lr_mult);
 spo_status spo_surrogate_nparams(const spo_surrogate *s, int64_t *n);

@@ -72,10 +72,11 @@ void free_workspace(spo_detail::Workspace &w) {
     cudaFree(w.slots);
     cudaFree(w.perm);
     cudaFree(w.sorted);
+    cudaFree(w.wrec);
     cudaFree(w.partials);
     cudaFree(w.vscratch);
     w.counts = w.offsets = w.keys = w.slots = w.perm = nullptr;
-    w.sorted = nullptr;
+    w.sorted = w.wrec = nullptr;
     w.partials = w.vscratch = nullptr;
     w.cap_partials = w.cap_vscratch = 0;
     w.cap_positions = w.cap_bins = 0;
@@ -102,8 +103,9 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
         cudaFree(w->slots);
         cudaFree(w->perm);
         cudaFree(w->sorted);
+        cudaFree(w->wrec);
         w->counts = w->offsets = w->keys = w->slots = w->perm = nullptr;
-        w->sorted = nullptr;
+        w->sorted = w->wrec = nullptr;
         w->cap_positions = w->cap_bins = 0;
         // counts: nbins + 1 ints (the last one the count kernel's ticket),
         // zero between calls (the count kernel clears what it used)
@@ -113,7 +115,8 @@ spo_status workspace_for(spo_set *s, cudaStream_t stream, int64_t P, spo_detail:
             cudaMalloc(&w->keys, sizeof(int) * cp) != cudaSuccess ||
             cudaMalloc(&w->slots, sizeof(int) * cp) != cudaSuccess ||
             cudaMalloc(&w->perm, sizeof(int) * cp) != cudaSuccess ||
-            cudaMalloc(&w->sorted, sizeof(float4) * cp) != cudaSuccess) {
+            cudaMalloc(&w->sorted, sizeof(float4) * cp) != cudaSuccess ||
+            cudaMalloc(&w->wrec, sizeof(float4) * spo_detail::kWeightRecordF4 * cp) != cudaSuccess) {
             cudaGetLastError();
             free_workspace(*w);
             return fail(SPO_ENOMEM, "cudaMalloc of binning scratch for %lld positions failed",

@@ -35,6 +35,7 @@ struct spo_batch {
     int *counts = nullptr, *offsets = nullptr;    // [total_bricks], [total_bricks + 1]
     int *keys = nullptr, *slots = nullptr;        // [max_positions]
     float4 *sorted = nullptr;                     // [max_positions]
+    float4 *wrec = nullptr;                       // [max_positions][11] weight records
     float **dst = nullptr;                        // [max_positions]
 
     // pinned staging of the item table, and the event after its last copy
@@ -90,7 +91,7 @@ __global__ void batch_scatter_kernel(const spo_work *__restrict__ items,
                                      const __grid_constant__ BatchParams bp,
                                      const int *__restrict__ keys, const int *__restrict__ slots,
                                      const int *__restrict__ offsets, float4 *__restrict__ sorted,
-                                     float **__restrict__ dst) {
+                                     float4 *__restrict__ wrec, float **__restrict__ dst) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Ptot;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int i = item_of[g];
@@ -98,8 +99,12 @@ __global__ void batch_scatter_kernel(const spo_work *__restrict__ items,
         const spo_work it = items[i];
         const BatchSetDesc &d = bp.sets[it.set];
         const int idx = offsets[keys[g]] + slots[g];
-        sorted[idx] = make_float4(__ldg(it.pos + 3 * l), __ldg(it.pos + 3 * l + 1),
-                                  __ldg(it.pos + 3 * l + 2), __int_as_float((int)g));
+        const float4 r = make_float4(__ldg(it.pos + 3 * l), __ldg(it.pos + 3 * l + 1),
+                                     __ldg(it.pos + 3 * l + 2), __int_as_float((int)g));
+        sorted[idx] = r;
+        // the position's basis weights, formed once for every orbital tile
+        spo_dev::make_weight_record(r, (int)g, d.gx, d.gy, d.gz,
+                                    wrec + (int64_t)idx * spo_detail::kWeightRecordF4);
         dst[idx] = it.out + l * d.rows * d.N;
     }
 }
@@ -113,6 +118,7 @@ void free_plan(spo_batch *b) {
     cudaFree(b->keys);
     cudaFree(b->slots);
     cudaFree(b->sorted);
+    cudaFree(b->wrec);
     cudaFree(b->dst);
     if (b->h_items) cudaFreeHost(b->h_items);
     if (b->h_start) cudaFreeHost(b->h_start);
@@ -196,11 +202,11 @@ spo_status queue_work(spo_batch *b, spo_kind kind, int nitems, int64_t Ptot, boo
     if (e == cudaSuccess) {
         batch_scatter_kernel<<<blocks, threads, 0, stream>>>(b->d_items, b->d_start, b->d_item_of, Ptot,
                                                              bp, b->keys, b->slots, b->offsets,
-                                                             b->sorted, b->dst);
+                                                             b->sorted, b->wrec, b->dst);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)
-        e = spo_detail::launch_brick_batch(b->storage, kind, b->tile, bp, b->offsets, b->sorted,
+        e = spo_detail::launch_brick_batch(b->storage, kind, b->tile, bp, b->offsets, b->wrec,
                                            b->dst, vec_out, b->status, stream);
     return e == cudaSuccess ? SPO_OK : cuda_fail(e, "batched evaluation launch");
 }
@@ -269,6 +275,7 @@ spo_status spo_batch_create(const spo_set *const *sets, int nsets, int64_t max_p
     if (e == cudaSuccess) e = cudaMalloc(&b->keys, sizeof(int) * P);
     if (e == cudaSuccess) e = cudaMalloc(&b->slots, sizeof(int) * P);
     if (e == cudaSuccess) e = cudaMalloc(&b->sorted, sizeof(float4) * P);
+    if (e == cudaSuccess) e = cudaMalloc(&b->wrec, sizeof(float4) * spo_detail::kWeightRecordF4 * P);
     if (e == cudaSuccess) e = cudaMalloc(&b->dst, sizeof(float *) * P);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(spo_work) * I);
     if (e == cudaSuccess) e = cudaMallocHost(&b->h_start, sizeof(int64_t) * (I + 1));

@@ -46,7 +46,7 @@ cudaError_t launch_batch_bin(const spo_work *items, const int64_t *item_start, i
 
 // The brick kernel over every (set, brick, tile) unit of the batch.
 cudaError_t launch_brick_batch(spo_dtype storage, spo_kind kind, int tile, const BatchParams &bp,
-                               const int *offsets, const float4 *sorted, float *const *dst,
+                               const int *offsets, const float4 *wrec, float *const *dst,
                                bool vec_out, unsigned int *status, cudaStream_t stream);
 
 // Allow the batched brick kernels their dynamic shared memory (host, once).

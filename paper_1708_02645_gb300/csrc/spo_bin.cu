@@ -10,7 +10,11 @@
 //                         the ticket) for the next call, so no block waits
 //                         on another and no memset is needed
 //   2. bin_scatter_kernel: perm[offsets[key] + slot] = position index, and
-//                         the position with its index in the same sorted slot
+//                         the position with its index in the same sorted slot;
+//                         when the workspace has room for them, also the
+//                         position's weight record (its 36 basis weights,
+//                         cells and index: the brick kernel's slot), formed
+//                         once here instead of once per orbital tile
 // (bin_scan_kernel is the stand-alone scan, used by the crowd binning.)
 //
 // The order inside a brick depends on atomic arrival order; every output of
@@ -27,6 +31,7 @@ using spo_detail::kBrick;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kCountThreads = 256;
+static_assert(kSlotF4 == spo_detail::kWeightRecordF4, "a weight record is one brick-kernel slot");
 
 // Exclusive scan of counts[0..n) into offsets[0..n] by one block of THREADS
 // threads, in chunks of THREADS * kScanItems with a running carry; with
@@ -122,13 +127,16 @@ bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis
 
 __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
                                    const int *__restrict__ slots, const int *__restrict__ offsets,
-                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P) {
+                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P,
+                                   GridAxis gx, GridAxis gy, GridAxis gz, float4 *__restrict__ wrec) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = offsets[keys[p]] + slots[p];
         perm[i] = (int)p;
-        sorted[i] = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
-                                __int_as_float((int)p));
+        const float4 r = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
+                                     __int_as_float((int)p));
+        sorted[i] = r;
+        if (wrec) make_weight_record(r, (int)p, gx, gy, gz, wrec + (int64_t)i * kSlotF4);
     }
 }
 
@@ -154,7 +162,8 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bin_scatter_kernel<<<blocks, threads, 0, stream>>>(pos, w.keys, w.slots, w.offsets, w.perm,
-                                                       w.sorted, P);
+                                                       w.sorted, P, grid_axis(nx), grid_axis(ny),
+                                                       grid_axis(nz), w.wrec);
     return cudaGetLastError();
 }
 

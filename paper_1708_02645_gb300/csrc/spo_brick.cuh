@@ -9,9 +9,12 @@
 // corner row is one conflict-free 8- or 16-byte shared load per thread for
 // FP32, 4 or 8 bytes for BF16/FP16); positions are read as sorted
 // (x, y, z, index) records written by the binning, one round ahead; each
-// position's 36 weights are formed once by three lanes of its group and
-// shared through a slot in shared memory (spo_device.cuh,
-// stage_axis_weights); the z -> y -> x reduction and its FMA order are
+// position's 36 weights, cells and index are formed once per batch by the
+// binning (a 176-byte weight record per position, spo_device.cuh
+// make_weight_record), and every orbital tile's CTA copies the records of
+// its positions into slots in shared memory, one round ahead (without
+// records, three lanes of a position's group form its slot); the
+// z -> y -> x reduction and its FMA order are
 // those of the gather kernel (spo_device.cuh), and outputs are scattered
 // back to each position's own rows with streaming stores.  With 32-orbital
 // tiles and at least two bricks along z, a CTA takes a z-adjacent pair of
@@ -74,12 +77,18 @@ constexpr size_t kSlotBytes = (size_t)(BrickShape<TILE>::threads / (TILE / V)) *
 // and its positions are the two bricks' contiguous ranges of the sorted
 // order, so each CTA evaluates twice as many positions per staged node and
 // per start-up.  The arithmetic per position is unchanged (same bits).
-template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false, bool PAIR = false>
+// REC: the binning formed every position's weight record (wrec), and each
+// orbital tile copies them into its slots; without REC the slots are formed
+// here from the sorted position records (the allocation-free entry point,
+// whose fixed scratch holds no records).
+template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false, bool PAIR = false,
+          bool REC = true>
 __global__ void __launch_bounds__(BrickShape<TILE>::threads, PAIR ? 3 : BrickShape<TILE>::ctas_per_sm)
 spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
                  int nby, int nbz, int ntiles, int64_t N, const int *__restrict__ offsets,
-                 const float4 *__restrict__ sorted, float *__restrict__ out, int eager,
-                 spo_detail::RatioArgs ra, unsigned int *__restrict__ status)
+                 const float4 *__restrict__ sorted, const float4 *__restrict__ wrec,
+                 float *__restrict__ out, int eager, spo_detail::RatioArgs ra,
+                 unsigned int *__restrict__ status)
 {
     static_assert(!RATIO || KIND == SPO_KIND_V, "ratios are formed from values");
     constexpr int NC = Rows<KIND>::value;
@@ -138,14 +147,39 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     const int wg0 = (int)(threadIdx.x >> 5) * (32 / TPP);   // first position group of this warp
     float4 *slot = wslots + (threadIdx.x / TPP) * kSlotF4;
     int i = begin + threadIdx.x / TPP;
-    // each round's position record (x, y, z, index) was loaded one round early
-    float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // Each round, lane q of a position's group brings parts q, q + TPP, ...
+    // of the position's weight slot: copies of the record the binning formed
+    // (REC), or else the slot formed here from the position record (x, y,
+    // z, index) in part 0.  Both are loaded one round early.
+    constexpr int NPART = REC ? (kSlotF4 + TPP - 1) / TPP : 1;
+    auto fetch = [&](int ii, float4 (&r)[NPART]) {
+        if (ii >= end) return;
+        if constexpr (REC) {
+#pragma unroll
+            for (int k = 0; k < NPART; ++k)
+                if (q + k * TPP < kSlotF4) r[k] = __ldg(wrec + (int64_t)ii * kSlotF4 + q + k * TPP);
+        } else {
+            r[0] = __ldg(sorted + ii);
+        }
+    };
+    float4 cur[NPART];
+#pragma unroll
+    for (int k = 0; k < NPART; ++k) cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    fetch(i, cur);
     bool ready = false;
     for (int ib = begin + wg0; ib < end; ib += PPR, i += PPR) {
-        const float4 nxt = i + PPR < end ? __ldg(sorted + i + PPR) : cur;
-        const int p = __float_as_int(cur.w);
+        float4 nxt[NPART];
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) nxt[k] = cur[k];
+        fetch(i + PPR, nxt);
         __syncwarp();   // the previous round's reads of the slots are done
-        stage_axis_weights(q, cur, gx, gy, gz, slot);
+        if constexpr (REC) {
+#pragma unroll
+            for (int k = 0; k < NPART; ++k)
+                if (q + k * TPP < kSlotF4) slot[q + k * TPP] = cur[k];
+        } else {
+            stage_axis_weights(q, cur[0], gx, gy, gz, slot);
+        }
         __syncwarp();
         if (!ready) {   // the first round's weights were formed while the copy flew
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_s, 0))) {
@@ -157,6 +191,7 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
         if (i < end) {
             Axis Y, Z;
             const int4 cells = *reinterpret_cast<const int4 *>(slot + 10);
+            const int p = cells.w;
             unpack4(slot[4], Y.w);
             unpack4(slot[5], Y.d);
             unpack4(slot[6], Y.dd);
@@ -195,7 +230,8 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
             if (o0 < N && (!RATIO || out != nullptr))
                 store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
         }
-        cur = nxt;
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) cur[k] = nxt[k];
     }
     if (!ready && threadIdx.x == 0) {
         // a thread with no position still must not leave while the copy
@@ -401,7 +437,7 @@ spo_brick_pipe_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, Grid
     }
 }
 
-template <typename T, int KIND, int TILE, int V>
+template <typename T, int KIND, int TILE, int V, bool REC = true>
 cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P, float *out,
                          cudaStream_t stream) {
     const int nbins = s->nbx * s->nby * s->nbz;
@@ -414,13 +450,13 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
                                  kSlotBytes<TILE, V>;
         const int64_t blocks = (int64_t)s->nbx * s->nby * ((s->nbz + 1) / 2) * ntiles;
         if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-        auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true, false, true>
-                              : spo_brick_kernel<T, KIND, TILE, V, false, false, true>;
+        auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true, false, true, REC>
+                              : spo_brick_kernel<T, KIND, TILE, V, false, false, true, REC>;
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemP);
         if (e != cudaSuccess) return e;
         kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmemP, stream>>>(
             s->block_map[2], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles,
-            s->N, w.offsets, w.sorted, out, eager,
+            s->N, w.offsets, w.sorted, w.wrec, out, eager,
             spo_detail::RatioArgs{}, s->status);
         return cudaGetLastError();
       }
@@ -428,14 +464,14 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
     constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16 + kSlotBytes<TILE, V>;
     const int64_t blocks = (int64_t)nbins * ntiles;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true>
-                          : spo_brick_kernel<T, KIND, TILE, V, false>;
+    auto kernel = vec_out ? spo_brick_kernel<T, KIND, TILE, V, true, false, false, REC>
+                          : spo_brick_kernel<T, KIND, TILE, V, false, false, false, REC>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, out, eager,
+        w.offsets, w.sorted, w.wrec, out, eager,
         spo_detail::RatioArgs{}, s->status);
     return cudaGetLastError();
 }
@@ -443,6 +479,7 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
 template <typename T, int TILE, int V>
 cudaError_t brick_ratio_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P,
                                float *out, const spo_detail::RatioArgs &ra, cudaStream_t stream) {
+    if (!w.wrec) return cudaErrorInvalidValue;   // ratio workspaces always hold weight records
     constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16 + kSlotBytes<TILE, V>;
     const int nbins = s->nbx * s->nby * s->nbz;
     const int ntiles = (int)((s->N + TILE - 1) / TILE);
@@ -457,7 +494,7 @@ cudaError_t brick_ratio_launch(const spo_set *s, const spo_detail::Workspace &w,
     const int eager = P >= 4 * (int64_t)nbins;
     kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
         map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, out, eager,
+        w.offsets, w.sorted, w.wrec, out, eager,
         ra, s->status);
     return cudaGetLastError();
 }
@@ -500,6 +537,9 @@ cudaError_t brick_typed(const spo_set *s, const spo_detail::Workspace &w, int64_
     if (s->brick_schedule == 1)
         return spo_detail::brick_tile_of(s) == 64 ? brick_pipe_launch<T, KIND, 64>(s, w, out, stream)
                                                   : brick_pipe_launch<T, KIND, 32>(s, w, out, stream);
+    // without weight records (the allocation-free scratch) one tuning serves:
+    // every tuning gives the same bits
+    if (!w.wrec) return brick_launch<T, KIND, 32, 4, false>(s, w, P, out, stream);
     const bool v4 = s->brick_vec == 4;
     if (spo_detail::brick_tile_of(s) == 64)
         return v4 ? brick_launch<T, KIND, 64, 4>(s, w, P, out, stream)

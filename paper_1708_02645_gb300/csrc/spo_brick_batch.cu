@@ -1,8 +1,9 @@
 // Brick kernel over a batch of walkers and orbital sets: one CTA per
 // (set, brick, orbital tile) unit of the whole batch.  The sets' tensor maps
 // and shapes arrive in one __grid_constant__ parameter block; positions come
-// as sorted records from the batch binning, each with the address of its own
-// output rows (every walker has its own output buffer).  The per-position
+// as weight records in sorted order from the batch binning (its basis
+// weights, formed once for every orbital tile), each with the address of its
+// own output rows (every walker has its own output buffer).  The per-position
 // arithmetic is the single-set brick kernel's (spo_device.cuh), so a
 // walker's outputs are bit-identical to an spo_eval of that walker alone.
 #include <cuda.h>
@@ -34,7 +35,7 @@ struct Shape {
 template <typename T, int KIND, int TILE, bool VEC_OUT>
 __global__ void __launch_bounds__(Shape<TILE>::threads, Shape<TILE>::ctas_per_sm)
 spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__restrict__ offsets,
-                       const float4 *__restrict__ sorted, float *const *__restrict__ dst,
+                       const float4 *__restrict__ wrec, float *const *__restrict__ dst,
                        unsigned int *status)
 {
     constexpr int NC = Rows<KIND>::value;
@@ -89,15 +90,32 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
     const int wg0 = (int)(threadIdx.x >> 5) * (32 / TPP);
     float4 *slot = wslots + (threadIdx.x / TPP) * kSlotF4;
     int i = begin + threadIdx.x / TPP;
-    float4 cur = i < end ? __ldg(sorted + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    // lane q of a position's group copies parts q, q + TPP, ... of the
+    // position's weight record (formed by the binning) into the slot, one
+    // round ahead
+    constexpr int NPART = (kSlotF4 + TPP - 1) / TPP;
+    auto fetch = [&](int ii, float4 (&r)[NPART]) {
+#pragma unroll
+        for (int k = 0; k < NPART; ++k)
+            if (q + k * TPP < kSlotF4) r[k] = __ldg(wrec + (int64_t)ii * kSlotF4 + q + k * TPP);
+    };
+    float4 cur[NPART];
+#pragma unroll
+    for (int k = 0; k < NPART; ++k) cur[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < end) fetch(i, cur);
     float *ocur = i < end ? dst[i] : nullptr;
     bool ready = false;
     for (int ib = begin + wg0; ib < end; ib += PPR, i += PPR) {
         const bool more = i + PPR < end;
-        const float4 nxt = more ? __ldg(sorted + i + PPR) : cur;
+        float4 nxt[NPART];
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) nxt[k] = cur[k];
+        if (more) fetch(i + PPR, nxt);
         float *onxt = more ? dst[i + PPR] : ocur;
         __syncwarp();   // the previous round's reads of the slots are done
-        stage_axis_weights(q, cur, d.gx, d.gy, d.gz, slot);
+#pragma unroll
+        for (int k = 0; k < NPART; ++k)
+            if (q + k * TPP < kSlotF4) slot[q + k * TPP] = cur[k];
         __syncwarp();
         if (!ready) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_s, 0))) {
@@ -128,7 +146,8 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
                                 acc);
             if (o0 < N) store_rows<NC, kVec, VEC_OUT>(ocur + o0, N, N - o0, acc);
         }
-        cur = nxt;
+#pragma unroll
+        for (int k = 0; k < NPART; ++k) cur[k] = nxt[k];
         ocur = onxt;
     }
     if (!ready && threadIdx.x == 0 && !mbar_wait_bounded(bar_s, 0)) atomicOr(status, 1u);
@@ -142,35 +161,35 @@ constexpr size_t batch_smem() {
 }
 
 template <typename T, int KIND, int TILE>
-cudaError_t launch_typed(const BatchParams &bp, const int *offsets, const float4 *sorted,
+cudaError_t launch_typed(const BatchParams &bp, const int *offsets, const float4 *wrec,
                          float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
     constexpr size_t kSmem = batch_smem<T, TILE>();
     auto kernel = vec_out ? spo_brick_batch_kernel<T, KIND, TILE, true>
                           : spo_brick_batch_kernel<T, KIND, TILE, false>;
     if (bp.total_units <= 0) return cudaSuccess;
-    kernel<<<(unsigned)bp.total_units, Shape<TILE>::threads, kSmem, stream>>>(bp, offsets, sorted, dst,
+    kernel<<<(unsigned)bp.total_units, Shape<TILE>::threads, kSmem, stream>>>(bp, offsets, wrec, dst,
                                                                              status);
     return cudaGetLastError();
 }
 
 template <typename T, int KIND>
-cudaError_t launch_tile(int tile, const BatchParams &bp, const int *offsets, const float4 *sorted,
+cudaError_t launch_tile(int tile, const BatchParams &bp, const int *offsets, const float4 *wrec,
                         float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
-    return tile == 64 ? launch_typed<T, KIND, 64>(bp, offsets, sorted, dst, vec_out, status, stream)
-                      : launch_typed<T, KIND, 32>(bp, offsets, sorted, dst, vec_out, status, stream);
+    return tile == 64 ? launch_typed<T, KIND, 64>(bp, offsets, wrec, dst, vec_out, status, stream)
+                      : launch_typed<T, KIND, 32>(bp, offsets, wrec, dst, vec_out, status, stream);
 }
 
 template <typename T>
 cudaError_t launch_kind(spo_kind kind, int tile, const BatchParams &bp, const int *offsets,
-                        const float4 *sorted, float *const *dst, bool vec_out, unsigned int *status,
+                        const float4 *wrec, float *const *dst, bool vec_out, unsigned int *status,
                         cudaStream_t stream) {
     switch (kind) {
         case SPO_KIND_V:
-            return launch_tile<T, SPO_KIND_V>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+            return launch_tile<T, SPO_KIND_V>(tile, bp, offsets, wrec, dst, vec_out, status, stream);
         case SPO_KIND_VGL:
-            return launch_tile<T, SPO_KIND_VGL>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+            return launch_tile<T, SPO_KIND_VGL>(tile, bp, offsets, wrec, dst, vec_out, status, stream);
         case SPO_KIND_VGH:
-            return launch_tile<T, SPO_KIND_VGH>(tile, bp, offsets, sorted, dst, vec_out, status, stream);
+            return launch_tile<T, SPO_KIND_VGH>(tile, bp, offsets, wrec, dst, vec_out, status, stream);
     }
     return cudaErrorInvalidValue;
 }
@@ -211,16 +230,16 @@ cudaError_t prepare_brick_batch() {
 }
 
 cudaError_t launch_brick_batch(spo_dtype storage, spo_kind kind, int tile, const BatchParams &bp,
-                               const int *offsets, const float4 *sorted, float *const *dst,
+                               const int *offsets, const float4 *wrec, float *const *dst,
                                bool vec_out, unsigned int *status, cudaStream_t stream) {
     switch (storage) {
         case SPO_F32:
-            return launch_kind<float>(kind, tile, bp, offsets, sorted, dst, vec_out, status, stream);
+            return launch_kind<float>(kind, tile, bp, offsets, wrec, dst, vec_out, status, stream);
         case SPO_BF16:
-            return launch_kind<__nv_bfloat16>(kind, tile, bp, offsets, sorted, dst, vec_out, status,
+            return launch_kind<__nv_bfloat16>(kind, tile, bp, offsets, wrec, dst, vec_out, status,
                                               stream);
         case SPO_F16:
-            return launch_kind<__half>(kind, tile, bp, offsets, sorted, dst, vec_out, status, stream);
+            return launch_kind<__half>(kind, tile, bp, offsets, wrec, dst, vec_out, status, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -437,15 +437,16 @@ __device__ __forceinline__ void window_reduce(const XAxis &X, const GridAxis &gx
     window_x_node<KIND, V, 3>(xw, xd, xdd, Y, Z, load, acc);
 }
 
-// Weight slot of one position (kSlotF4 float4 in shared memory), used by
-// the brick kernels: x-node weights (w, w', w'', 0) for nodes 0..3, then
-// y's w[4], w'[4], w''[4], then z's, then the cells (x, y, z, -) as ints.
-// Lanes 0, 1 and 2 of a position's group each reduce one axis and form its
-// four nodes' weights (reduce_axis and node_weights, the functions every
-// kernel uses, so the bits are those of the gather kernel); the whole group
-// then reads them.  Forming the 36 weights once per position instead of
-// once per lane takes about 100 scalar FP32 operations per lane and
-// position off the FMA pipe.  A slot is 176 bytes (44 words), so the four
+// Weight slot of one position (kSlotF4 float4), used by the brick kernels:
+// x-node weights (w, w', w'', 0) for nodes 0..3, then y's w[4], w'[4],
+// w''[4], then z's, then the cells (x, y, z) and the position's index as
+// ints.  The binning can form the slots of all positions once
+// (make_weight_record, one thread per position) so that every orbital tile
+// only copies them; otherwise lanes 0, 1 and 2 of a position's group each
+// reduce one axis and form its four nodes' weights (stage_axis_weights) and
+// the group reads them back.  Either way the weights come from reduce_axis
+// and node_weights, the functions every kernel uses, so the bits are those
+// of the gather kernel.  A slot is 176 bytes (44 words), so the four
 // 16-byte reads of a warp's four groups fall in disjoint banks.
 constexpr int kSlotF4 = 11;
 
@@ -453,19 +454,49 @@ __device__ __forceinline__ void unpack4(const float4 &r, float (&v)[4]) {
     v[0] = r.x; v[1] = r.y; v[2] = r.z; v[3] = r.w;
 }
 
-__device__ __forceinline__ void stage_axis_weights(int q, const float4 &r, const GridAxis &gx,
-                                                   const GridAxis &gy, const GridAxis &gz,
-                                                   float4 *slot) {
-    const int a = q < 3 ? q : 0;   // lanes 3.. of the group repeat the x axis and store nothing
-    const GridAxis g = a == 0 ? gx : (a == 1 ? gy : gz);
-    const float u = a == 0 ? r.x : (a == 1 ? r.y : r.z);
-    int cell;
-    float t, w[4], d[4], dd[4];
+// Cell, and the weights of the four window nodes, of coordinate u on axis g.
+__device__ __forceinline__ void axis_weights(float u, const GridAxis &g, int &cell, float (&w)[4],
+                                             float (&d)[4], float (&dd)[4]) {
+    float t;
     reduce_axis(u, g, cell, t);
     node_weights<0>(t, g, w[0], d[0], dd[0]);
     node_weights<1>(t, g, w[1], d[1], dd[1]);
     node_weights<2>(t, g, w[2], d[2], dd[2]);
     node_weights<3>(t, g, w[3], d[3], dd[3]);
+}
+
+// The whole slot of position p at r = (x, y, z), formed by one thread.
+__device__ __forceinline__ void make_weight_record(const float4 &r, int p, const GridAxis &gx,
+                                                   const GridAxis &gy, const GridAxis &gz,
+                                                   float4 *__restrict__ rec) {
+    int cx, cy, cz;
+    float w[4], d[4], dd[4];
+    axis_weights(r.x, gx, cx, w, d, dd);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) rec[n] = make_float4(w[n], d[n], dd[n], 0.0f);
+    axis_weights(r.y, gy, cy, w, d, dd);
+    rec[4] = make_float4(w[0], w[1], w[2], w[3]);
+    rec[5] = make_float4(d[0], d[1], d[2], d[3]);
+    rec[6] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+    axis_weights(r.z, gz, cz, w, d, dd);
+    rec[7] = make_float4(w[0], w[1], w[2], w[3]);
+    rec[8] = make_float4(d[0], d[1], d[2], d[3]);
+    rec[9] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+    rec[10] = make_float4(__int_as_float(cx), __int_as_float(cy), __int_as_float(cz), __int_as_float(p));
+}
+
+// Lane q of a position's group forms its part of the slot from the
+// position record r = (x, y, z, index bits): lanes 0, 1, 2 the x, y, z axes
+// (and lane 0 the index); lanes 3.. repeat the x axis and store nothing.
+__device__ __forceinline__ void stage_axis_weights(int q, const float4 &r, const GridAxis &gx,
+                                                   const GridAxis &gy, const GridAxis &gz,
+                                                   float4 *slot) {
+    const int a = q < 3 ? q : 0;
+    const GridAxis g = a == 0 ? gx : (a == 1 ? gy : gz);
+    const float u = a == 0 ? r.x : (a == 1 ? r.y : r.z);
+    int cell;
+    float w[4], d[4], dd[4];
+    axis_weights(u, g, cell, w, d, dd);
     if (q == 0) {
 #pragma unroll
         for (int n = 0; n < 4; ++n) slot[n] = make_float4(w[n], d[n], dd[n], 0.0f);
@@ -476,6 +507,7 @@ __device__ __forceinline__ void stage_axis_weights(int q, const float4 &r, const
         s[2] = make_float4(dd[0], dd[1], dd[2], dd[3]);
     }
     if (q < 3) reinterpret_cast<int *>(slot + 10)[q] = cell;
+    if (q == 0) reinterpret_cast<int *>(slot + 10)[3] = __float_as_int(r.w);
 }
 
 // window_reduce with the x-node weights taken from xs[A] = (w, w', w'', -)

@@ -17,6 +17,8 @@ namespace spo_detail {
 // kernel stages the (kBrick + 3)^3 table rows a brick's windows touch.
 constexpr int kBrick = 4;
 constexpr int kBlockEdge = kBrick + 3;
+// float4 per weight record (a position's 36 basis weights, cells and index)
+constexpr int kWeightRecordF4 = 11;
 
 // Scratch of the binned path for one stream: brick counts and offsets, one
 // key and slot per position, the position permutation sorted by brick, and
@@ -29,6 +31,8 @@ struct Workspace {
     int *slots = nullptr;     // [P]
     int *perm = nullptr;      // [P]
     float4 *sorted = nullptr; // [P]
+    float4 *wrec = nullptr;   // [P][11] weight records in sorted order, or nullptr (the
+                              // brick kernel then forms the weights itself)
     float *partials = nullptr;   // [ratio tiles][P] partial dot products (ratios)
     float *vscratch = nullptr;   // [P][N] values for the unfused ratio path
     size_t cap_partials = 0, cap_vscratch = 0;   // floats

@@ -697,6 +697,7 @@ struct spo_surrogate {
     int64_t adam_t = 0;
     float beta1 = 0.9f, beta2 = 0.99f, eps = 1e-15f;
     float grid_lr_mult = 1.0f;   // the grid's learning rate relative to the perceptron's
+    float level_lr_power = 0.0f; // level l's grid rate is further scaled by (R_0 / R_l)^power
 
     // inference copies
     __half *grid16 = nullptr;
@@ -1347,10 +1348,21 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
             const float b1 = s->beta1, b2 = s->beta2;
             const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->adam_t));
             const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->adam_t));
-            // the grid (the first grid_n parameters) and the perceptron may
-            // take different rates
-            adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n,
-                                                               lr * s->grid_lr_mult, b1, b2, s->eps, c1, c2);
+            // the grid (the first grid_n parameters, level by level) and the
+            // perceptron may take different rates
+            if (s->level_lr_power == 0.0f) {
+                adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n,
+                                                                   lr * s->grid_lr_mult, b1, b2, s->eps, c1, c2);
+            } else {
+                const int64_t nlev = (int64_t)s->lv.table * s->lv.features;
+                for (int l = 0; l < s->lv.levels; ++l) {
+                    const float scale = (float)std::pow((double)s->lv.R[0] / s->lv.R[l], (double)s->level_lr_power);
+                    const int64_t o = l * nlev;
+                    adam_kernel<<<blocks_for(nlev), 256, 0, st>>>(s->param + o, s->grad + o, s->m1 + o, s->m2 + o,
+                                                                  nlev, lr * s->grid_lr_mult * scale, b1, b2,
+                                                                  s->eps, c1, c2);
+                }
+            }
             const int64_t nm = s->nparam - s->grid_n;
             adam_kernel<<<blocks_for(nm), 256, 0, st>>>(s->param + s->grid_n, s->grad + s->grid_n,
                                                         s->m1 + s->grid_n, s->m2 + s->grid_n, nm, lr, b1, b2,
@@ -1381,6 +1393,14 @@ spo_status spo_surrogate_set_optimizer(spo_surrogate *s, float beta1, float beta
     s->beta2 = beta2;
     s->eps = eps;
     s->grid_lr_mult = grid_lr_mult;
+    return SPO_OK;
+}
+
+spo_status spo_surrogate_set_level_lr(spo_surrogate *s, float power) {
+    fail(SPO_OK, "");
+    if (!s) return fail(SPO_EINVAL, "surrogate is NULL");
+    if (!(power >= 0.0f && power <= 4.0f)) return fail(SPO_EINVAL, "need 0 <= power <= 4");
+    s->level_lr_power = power;
     return SPO_OK;
 }
 

@@ -67,6 +67,7 @@ SIGNATURES = [
     ("spo_surrogate_grad", _INT, [_P, _P, _P, _I64, _P, _INT, ctypes.POINTER(ctypes.c_float), _P, _P,
                                   _P, _P]),
     ("spo_surrogate_set_train_precision", _INT, [_P, _INT]),
+    ("spo_surrogate_set_level_lr", _INT, [_P, ctypes.c_float]),
     ("spo_surrogate_set_optimizer", _INT, [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                            ctypes.c_float]),
     ("spo_surrogate_nparams", _INT, [_P, ctypes.POINTER(_I64)]),
@@ -610,6 +611,10 @@ class Surrogate:
         """1: training products on the tensor cores (BF16), 0: FP32."""
         _check(load().spo_surrogate_set_train_precision(self._h, int(precision)),
                "spo_surrogate_set_train_precision")
+
+    def set_level_lr(self, power: float):
+        """Scale the grid's rate of level l by (R_0 / R_l)^power."""
+        _check(load().spo_surrogate_set_level_lr(self._h, float(power)), "spo_surrogate_set_level_lr")
 
     def set_optimizer(self, beta1=0.9, beta2=0.99, eps=1e-15, grid_lr_mult=1.0):
         _check(load().spo_surrogate_set_optimizer(self._h, float(beta1), float(beta2), float(eps),

@@ -112,6 +112,7 @@ def test_newer_entry_points_reject_bad_arguments_before_cuda(lib):
     assert lib.spo_surrogate_footprint(None, ctypes.byref(b)) == 1
     assert lib.spo_surrogate_set_optimizer(None, 0.9, 0.99, 1e-15, 1.0) == 1
     assert lib.spo_surrogate_set_train_precision(None, 1) == 1
+    assert lib.spo_surrogate_set_level_lr(None, 2.0) == 1
     n = ctypes.c_int64()
     assert lib.spo_surrogate_nparams(None, ctypes.byref(n)) == 1
     assert lib.spo_surrogate_destroy(None) == 0
