@@ -30,7 +30,7 @@ using spo_detail::kBrick;
 
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
-constexpr int kCountThreads = 256;
+constexpr int kCountThreads = 1024;
 static_assert(kSlotF4 == spo_detail::kWeightRecordF4, "a weight record is one brick-kernel slot");
 
 // Exclusive scan of counts[0..n) into offsets[0..n] by one block of THREADS

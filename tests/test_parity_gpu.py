@@ -157,6 +157,33 @@ def test_degenerate_position_clouds(spo_lib, oracle_lib):
                    algos=["auto"] + ALGOS)
 
 
+def column_clusters(grid, nclusters, nuniform, seed):
+    """Positions in clusters along z columns of cells: per cluster, members
+    in the cluster's cell (twice), 1, 2 and 3 cells above it and 1 below
+    (each at its own fraction within the cell): many positions share a
+    cell or a column of one brick; plus uniform positions.  FP32."""
+    n = np.array(grid, dtype=np.float64)
+    u = inputs.uniform01(seed, 3 * nclusters).reshape(nclusters, 3)
+    base = np.floor(u * n)
+    dz = np.array([0, 0, 1, 2, 3, -1], dtype=np.float64)
+    f = inputs.uniform01(seed + 1, nclusters * len(dz) * 3).reshape(nclusters, len(dz), 3)
+    cells = np.repeat(base[:, None, :], len(dz), axis=1)
+    cells[:, :, 2] += dz
+    pos = ((cells + f) / n).reshape(-1, 3)
+    return np.concatenate([pos, inputs.uniform_positions(nuniform, seed + 2).astype(np.float64)]).astype(np.float32)
+
+
+@pytest.mark.parametrize("grid,N,storage", [((24, 20, 28), 40, "f32"), ((16, 16, 32), 96, "f32"),
+                                            ((24, 20, 28), 40, "bf16")])
+def test_values_on_column_clusters(spo_lib, oracle_lib, grid, N, storage):
+    """Clustered positions (an odd number of bricks along z in the first
+    grid, a ragged last orbital tile for N = 40): every strategy bit for bit
+    and the oracle element by element."""
+    pos = column_clusters(grid, 500, 1500, 71)
+    c = inputs.plane_wave_coefs(*grid, N, seed=72)
+    check_case(spo_lib, c, pos, "v", storage, algos=ALGOS, what=f"clusters {grid} N={N}")
+
+
 def test_binning_reused_for_several_kinds(spo_lib):
     """spo_bin once, then V, VGL and VGH from the same binning (the ratio and
     derivative evaluations of one move) equal the one-call results."""

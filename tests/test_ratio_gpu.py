@@ -132,3 +132,25 @@ def test_ratio_nlpp_quadrature_batch_sampled(spo_lib, oracle_lib):
         assert spo_lib.device_status() == 0
     sample = np.sort(np.unique((inputs.uniform01(67, 1024) * len(pts)).astype(np.int64)))
     check(got.cpu().numpy()[sample], c, pts[sample], rows, row_of[sample])
+
+
+def test_ratio_on_column_clusters(spo_lib, oracle_lib):
+    """The fused ratio on clustered positions (rows shared through row_of)
+    against the oracle; its values equal the gather kernel's."""
+    import test_parity_gpu as tp
+    t = torch()
+    grid, N = (24, 20, 28), 72
+    c = inputs.plane_wave_coefs(*grid, N, seed=73).astype(np.float32)
+    pos = tp.column_clusters(grid, 500, 1500, 74)
+    P, nrows = pos.shape[0], 300
+    rows = (2.0 * inputs.uniform01(75, nrows * N) - 1.0).astype(np.float32).reshape(nrows, N)
+    row_of = (inputs.uniform01(76, P) * nrows).astype(np.int32)
+    with spo_lib.OrbitalSet(c) as s:
+        p = t.from_numpy(pos).cuda()
+        v = t.empty((P, N), device="cuda")
+        got = s.eval_ratio(p, t.from_numpy(rows).cuda(), t.from_numpy(row_of).cuda(), v_out=v)
+        ref_v = s.eval(p, "v", algo="gather")
+        t.cuda.synchronize()
+        assert spo_lib.device_status() == 0
+        assert t.equal(v, ref_v)
+    check(got.cpu().numpy(), c, pos, rows, row_of)
