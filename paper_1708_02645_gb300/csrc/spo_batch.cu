@@ -132,10 +132,15 @@ BatchParams make_params(const spo_batch *b, spo_kind kind, int tile, int64_t Pto
     BatchParams bp;
     memset(&bp, 0, sizeof(bp));
     bp.nsets = b->nsets;
+    // 32-orbital tiles run on z-adjacent pairs of bricks when every set has
+    // the pair map (as the single-set kernel does)
+    bp.pair = tile == 32 ? 1 : 0;
+    for (int k = 0; k < b->nsets; ++k)
+        if (!b->sets[k]->has_pair_map) bp.pair = 0;
     int brick = 0, unit = 0;
     for (int k = 0; k < b->nsets; ++k) {
         const spo_set *s = b->sets[k];
-        bp.maps[k] = s->block_map[tile == 64 ? 1 : 0];
+        bp.maps[k] = s->block_map[bp.pair ? 2 : (tile == 64 ? 1 : 0)];
         BatchSetDesc &d = bp.sets[k];
         d.gx = spo_dev::grid_axis(s->nx);
         d.gy = spo_dev::grid_axis(s->ny);
@@ -149,7 +154,7 @@ BatchParams make_params(const spo_batch *b, spo_kind kind, int tile, int64_t Pto
         d.rows = spo_rows(kind);
         d.N = s->N;
         brick += d.nbins;
-        unit += d.nbins * d.ntiles;
+        unit += (bp.pair ? s->nbx * s->nby * ((s->nbz + 1) / 2) : d.nbins) * d.ntiles;
     }
     bp.total_bricks = brick;
     bp.total_units = unit;

@@ -19,7 +19,7 @@ struct BatchSetDesc {
     int nbins;        // bricks of this set
     int brick_base;   // first global brick of this set
     int ntiles;       // orbital tiles of the brick kernel
-    int unit_base;    // first (brick, tile) unit of this set
+    int unit_base;    // first (brick or brick pair, tile) unit of this set
     int rows;         // output rows per position (1, 5 or 10)
     int pad;
     int64_t N;
@@ -34,6 +34,7 @@ struct BatchParams {
     int total_units;
     int total_bricks;
     int eager;
+    int pair;         // units are z-adjacent pairs of bricks (32-orbital tiles, pair maps)
 };
 
 // Binning of all walkers' positions into the global brick space: counts,

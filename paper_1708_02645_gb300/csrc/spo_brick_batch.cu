@@ -32,17 +32,23 @@ struct Shape {
     static constexpr int ctas_per_sm = TILE >= 64 ? 2 : 4;
 };
 
-template <typename T, int KIND, int TILE, bool VEC_OUT>
-__global__ void __launch_bounds__(Shape<TILE>::threads, Shape<TILE>::ctas_per_sm)
+// PAIR (32-orbital tiles, every set with brick-pair maps): a unit is a
+// z-adjacent pair of bricks, its block one 7 x 7 x 11-node box and its
+// positions the two bricks' contiguous ranges of the sorted order, as in the
+// single-set kernel's pair form (3 CTAs per SM).
+template <typename T, int KIND, int TILE, bool VEC_OUT, bool PAIR = false>
+__global__ void __launch_bounds__(Shape<TILE>::threads, PAIR ? 3 : Shape<TILE>::ctas_per_sm)
 spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__restrict__ offsets,
                        const float4 *__restrict__ wrec, float *const *__restrict__ dst,
                        unsigned int *status)
 {
+    static_assert(!PAIR || TILE == 32, "brick pairs with 32-orbital tiles");
     constexpr int NC = Rows<KIND>::value;
     constexpr int kThreads = Shape<TILE>::threads;
     constexpr int TPP = TILE / kVec;
     constexpr int PPR = kThreads / TPP;
-    constexpr uint32_t kBytes = kBlockRows * TILE * sizeof(T);
+    constexpr int kBZ = PAIR ? 2 * kBrick + 3 : kBlockEdge;   // block nodes along z
+    constexpr uint32_t kBytes = kBlockEdge * kBlockEdge * kBZ * TILE * sizeof(T);
     extern __shared__ __align__(1024) unsigned char smem[];
     T *block = reinterpret_cast<T *>(smem);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kBytes);
@@ -53,15 +59,18 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
     while (s + 1 < bp.nsets && unit >= bp.sets[s + 1].unit_base) ++s;
     const BatchSetDesc &d = bp.sets[s];
     const int local = unit - d.unit_base;
-    const int lbrick = local / d.ntiles, tile = local - lbrick * d.ntiles;
-    const int bz = lbrick % d.nbz, by = (lbrick / d.nbz) % d.nby, bx = lbrick / (d.nbz * d.nby);
-    const int gbrick = d.brick_base + lbrick;
+    const int lbrick = local / d.ntiles, tile = local - lbrick * d.ntiles;   // brick (or pair) of the set
+    const int nbzu = PAIR ? (d.nbz + 1) / 2 : d.nbz;
+    const int bzu = lbrick % nbzu, by = (lbrick / nbzu) % d.nby, bx = lbrick / (nbzu * d.nby);
+    const int bz = PAIR ? 2 * bzu : bzu;
+    const int gbrick = d.brick_base + (bx * d.nby + by) * d.nbz + bz;
+    const int gend = gbrick + ((PAIR && bz + 1 < d.nbz) ? 2 : 1);
     const uint32_t bar_s = smem_addr(bar);
 
     int begin = 0, end = 0;
     if (!bp.eager) {
         begin = __ldg(offsets + gbrick);
-        end = __ldg(offsets + gbrick + 1);
+        end = __ldg(offsets + gend);
         if (begin == end) return;
     }
     if (threadIdx.x == 0) {
@@ -74,7 +83,7 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
     }
     if (bp.eager) {
         begin = __ldg(offsets + gbrick);
-        end = __ldg(offsets + gbrick + 1);
+        end = __ldg(offsets + gend);
     }
     __syncthreads();
     if (begin == end) {
@@ -135,13 +144,13 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
             unpack4(slot[9], Z.dd);
             const int lx = min(max(cells.x - bx * kBrick, 0), kBrick - 1);
             const int ly = min(max(cells.y - by * kBrick, 0), kBrick - 1);
-            const int lz = min(max(cells.z - bz * kBrick, 0), kBrick - 1);
-            const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + q * kVec;
+            const int lz = min(max(cells.z - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
+            const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + q * kVec;
             float acc[NC][kVec];
             window_reduce_staged<KIND, kVec, true>(slot, Y, Z,
                                 [&](int a, int b, int g, float *v) {
                                     load_coefs<T, kVec, false>(
-                                        base + ((a * kBlockEdge + b) * kBlockEdge + g) * TILE, v);
+                                        base + ((a * kBlockEdge + b) * kBZ + g) * TILE, v);
                                 },
                                 acc);
             if (o0 < N) store_rows<NC, kVec, VEC_OUT>(ocur + o0, N, N - o0, acc);
@@ -155,18 +164,29 @@ spo_brick_batch_kernel(const __grid_constant__ BatchParams bp, const int *__rest
 
 // dynamic shared memory: the 7x7x7-node block, the barrier, one weight slot
 // per position of a round
-template <typename T, int TILE>
+template <typename T, int TILE, bool PAIR = false>
 constexpr size_t batch_smem() {
-    return (size_t)kBlockRows * TILE * sizeof(T) + 16 + (size_t)(Shape<TILE>::threads / (TILE / kVec)) * kSlotF4 * 16;
+    return (size_t)kBlockEdge * kBlockEdge * (PAIR ? 2 * kBrick + 3 : kBlockEdge) * TILE * sizeof(T) + 16 +
+           (size_t)(Shape<TILE>::threads / (TILE / kVec)) * kSlotF4 * 16;
 }
 
 template <typename T, int KIND, int TILE>
 cudaError_t launch_typed(const BatchParams &bp, const int *offsets, const float4 *wrec,
                          float *const *dst, bool vec_out, unsigned int *status, cudaStream_t stream) {
+    if (bp.total_units <= 0) return cudaSuccess;
+    if constexpr (TILE == 32) {
+        if (bp.pair) {
+            constexpr size_t kSmemP = batch_smem<T, 32, true>();
+            auto kernel = vec_out ? spo_brick_batch_kernel<T, KIND, 32, true, true>
+                                  : spo_brick_batch_kernel<T, KIND, 32, false, true>;
+            kernel<<<(unsigned)bp.total_units, Shape<32>::threads, kSmemP, stream>>>(bp, offsets, wrec, dst,
+                                                                                     status);
+            return cudaGetLastError();
+        }
+    }
     constexpr size_t kSmem = batch_smem<T, TILE>();
     auto kernel = vec_out ? spo_brick_batch_kernel<T, KIND, TILE, true>
                           : spo_brick_batch_kernel<T, KIND, TILE, false>;
-    if (bp.total_units <= 0) return cudaSuccess;
     kernel<<<(unsigned)bp.total_units, Shape<TILE>::threads, kSmem, stream>>>(bp, offsets, wrec, dst,
                                                                              status);
     return cudaGetLastError();
@@ -207,6 +227,11 @@ cudaError_t prepare_kind() {
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 64, false>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+    const int sp = (int)batch_smem<T, 32, true>();
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, true, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sp);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(spo_brick_batch_kernel<T, KIND, 32, false, true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, sp);
     return e;
 }
 
