@@ -370,7 +370,8 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  * spo_surrogate_eval(s, kind, pos, P, out, precision, stream): kind V or
  *   VGL; precision 0 evaluates the FP32 master parameters (CUDA cores),
  *   precision 1 the inference copies (FP16 grid, BF16 weights and
- *   activations, FP32 accumulation on the tcgen05 tensor cores).
+ *   activations, FP32 accumulation on the tcgen05 tensor cores; out must
+ *   be 32-byte aligned, else SPO_EINVAL).
  * spo_surrogate_grad(s, pos, target, P, channel_weights, precision, &loss,
  *   grid, W, b, stream): loss and its gradient with respect to every FP32
  *   master parameter for P device positions [P][3] and device targets

@@ -1229,6 +1229,9 @@ spo_status spo_surrogate_eval(spo_surrogate *s, spo_kind kind, const float *pos,
     DeviceGuard guard(s->device);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (precision == 1 && s->use_tc) {   // encoding kernel + one fused launch
+        // the fused kernel writes 32-byte vectors (N is a multiple of 16)
+        if (reinterpret_cast<uintptr_t>(out) & 31u)
+            return fail(SPO_EINVAL, "precision 1 needs out 32-byte aligned");
         const bool vo = kind == SPO_KIND_V;
         const size_t need = spo_detail::surrogate_feature_bytes(P, vo, s->num_sms);
         if (need > s->feat_cap) {

@@ -179,6 +179,17 @@ def test_errors_and_empty(spo_lib):
             s.eval(pos, kind="vgh")
         with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
             s.eval(pos, precision=2)
+    # the fused tensor-core kernel writes 32-byte vectors: a misaligned output
+    # is refused (this spec qualifies for it: 16 encoded features, width 128)
+    tc = S.SurrogateSpec(levels=8, log2_table=12, features=2, r_min=2, r_max=16, hidden=128, layers=2, N=32)
+    with spo_lib.Surrogate(tc, seed=0) as s:
+        pos = t.rand((4, 3), device="cuda")
+        base = t.empty(4 * 5 * tc.N + 8, device="cuda")
+        with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
+            s.eval(pos, out=base[4:4 + 4 * 5 * tc.N].view(4, 5, tc.N), precision=1)
+        ok = s.eval(pos, out=base[8:8 + 4 * 5 * tc.N].view(4, 5, tc.N), precision=1)
+        t.cuda.synchronize()
+        assert t.equal(ok, s.eval(pos, precision=1))
     bad = S.SurrogateSpec(levels=0)
     with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
         spo_lib.Surrogate(bad)
