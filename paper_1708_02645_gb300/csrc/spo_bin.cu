@@ -22,6 +22,7 @@
 #include "spo_batch.h"
 #include "spo_device.cuh"
 #include "spo_internal.h"
+#include "spo_tma.cuh"
 
 namespace {
 
@@ -119,16 +120,22 @@ bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis
         last = atomicAdd(counts + nbins, 1) == (int)gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
+    if (!last) {
+        grid_dependents_launch();   // after this block's writes (see the scatter)
+        return;
+    }
     __threadfence();   // every block's counts are visible to this one
     block_scan_counts<kCountThreads, true>(counts, offsets, nbins);
     if (threadIdx.x == 0) counts[nbins] = 0;
+    __syncthreads();
+    grid_dependents_launch();
 }
 
 __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
                                    const int *__restrict__ slots, const int *__restrict__ offsets,
                                    int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P,
                                    GridAxis gx, GridAxis gy, GridAxis gz, float4 *__restrict__ wrec) {
+    grid_dependency_wait();     // the counts, keys, slots and offsets are complete
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = offsets[keys[p]] + slots[p];
@@ -138,6 +145,11 @@ __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__r
         sorted[i] = r;
         if (wrec) make_weight_record(r, (int)p, gx, gy, gz, wrec + (int64_t)i * kSlotF4);
     }
+    // the brick kernel's CTAs may be scheduled (they issue their table copies
+    // and wait for this grid); the CTA triggers after all its threads'
+    // writes, so the wait covers them where a dependency ends at the trigger
+    __syncthreads();
+    grid_dependents_launch();
 }
 
 }  // namespace
@@ -161,10 +173,21 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
                                                      nbz, nbins, w.counts, w.offsets, w.keys, w.slots);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bin_scatter_kernel<<<blocks, threads, 0, stream>>>(pos, w.keys, w.slots, w.offsets, w.perm,
-                                                       w.sorted, P, grid_axis(nx), grid_axis(ny),
-                                                       grid_axis(nz), w.wrec);
-    return cudaGetLastError();
+    // programmatic dependent launch: the scatter is scheduled while the
+    // count kernel runs and waits for it in the kernel
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, bin_scatter_kernel, pos, (const int *)w.keys, (const int *)w.slots,
+                              (const int *)w.offsets, w.perm, w.sorted, P, grid_axis(nx), grid_axis(ny),
+                              grid_axis(nz), w.wrec);
 }
 
 }  // namespace spo_detail

@@ -39,6 +39,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <utility>
 
 #include "spo_batch.h"
 #include "spo_device.cuh"
@@ -116,8 +117,12 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     // With `eager` (bricks hold several positions on average) the copy is
     // issued first and the brick's position range is read while it flies;
     // otherwise empty bricks are skipped before any copy.
+    // Launched as a programmatic dependent of the binning: the table block
+    // depends only on the table, so its copy is issued before waiting for
+    // the binning (offsets, sorted records, weight records).
     int begin = 0, end = 0;
     if (!eager) {
+        grid_dependency_wait();
         begin = __ldg(offsets + b0);
         end = __ldg(offsets + b1);
         if (begin == end) return;
@@ -130,6 +135,7 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
         tma_load_4d(smem_addr(block), &map, bar_s, tile * TILE, bz * kBrick, by * kBrick, bx * kBrick);
     }
     if (eager) {
+        grid_dependency_wait();
         begin = __ldg(offsets + b0);
         end = __ldg(offsets + b1);
     }
@@ -437,6 +443,25 @@ spo_brick_pipe_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, Grid
     }
 }
 
+// Launch as a programmatic dependent of the previous kernel in the stream
+// (the binning's scatter): CTAs may be scheduled while it finishes and wait
+// for it in the kernel (grid_dependency_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                             cudaStream_t stream, Args &&...args) {
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T, int KIND, int TILE, int V, bool REC = true>
 cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64_t P, float *out,
                          cudaStream_t stream) {
@@ -454,11 +479,10 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
                               : spo_brick_kernel<T, KIND, TILE, V, false, false, true, REC>;
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemP);
         if (e != cudaSuccess) return e;
-        kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmemP, stream>>>(
-            s->block_map[2], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles,
-            s->N, w.offsets, w.sorted, w.wrec, out, eager,
-            spo_detail::RatioArgs{}, s->status);
-        return cudaGetLastError();
+        return launch_dependent(kernel, (unsigned)blocks, BrickShape<TILE>::threads, kSmemP, stream,
+                                s->block_map[2], grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby,
+                                s->nbz, ntiles, s->N, w.offsets, w.sorted, w.wrec, out, eager,
+                                spo_detail::RatioArgs{}, s->status);
       }
     }
     constexpr size_t kSmem = (size_t)kBlockRows * TILE * sizeof(T) + 16 + kSlotBytes<TILE, V>;
@@ -469,11 +493,9 @@ cudaError_t brick_launch(const spo_set *s, const spo_detail::Workspace &w, int64
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     if (e != cudaSuccess) return e;
     const CUtensorMap &map = s->block_map[TILE == 64 ? 1 : 0];
-    kernel<<<(unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream>>>(
-        map, grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
-        w.offsets, w.sorted, w.wrec, out, eager,
-        spo_detail::RatioArgs{}, s->status);
-    return cudaGetLastError();
+    return launch_dependent(kernel, (unsigned)blocks, BrickShape<TILE>::threads, kSmem, stream, map,
+                            grid_axis(s->nx), grid_axis(s->ny), grid_axis(s->nz), s->nby, s->nbz, ntiles, s->N,
+                            w.offsets, w.sorted, w.wrec, out, eager, spo_detail::RatioArgs{}, s->status);
 }
 
 template <typename T, int TILE, int V>
