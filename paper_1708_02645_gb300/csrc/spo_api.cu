@@ -146,17 +146,16 @@ spo_status ensure_floats(float **buf, size_t *cap, size_t need) {
 }
 
 // The strategy AUTO takes (without a tuned choice), by the mean number of
-// positions per brick r = P / bricks.  Measured crossovers (NiO-64 and
-// NiO-32 shapes, FP32): below r = 1.5 the gather kernel in input order wins
-// (no binning, little reuse to gain); a staged block pays for itself once a
-// brick holds enough positions to amortise it against the arithmetic: r = 3
-// for VGH (656 flop per evaluation), 8 for VGL, 12 for V (the kernel whose
-// cost is shared-memory reads); in between, the gather kernel in binned
-// order (L2 reuse without staging) is fastest.
+// positions per brick r = P / bricks.  Measured crossovers (NiO-64 shape,
+// FP32, per call with the binning): below r = 1.5 the gather kernel in
+// input order wins (no binning, little reuse to gain); a staged block pays
+// for itself once a brick holds enough positions to amortise it: r = 5 for
+// VGH, 7 for VGL, 8 for V; in between, the gather kernel in binned order
+// (L2 reuse without staging) is fastest.
 spo_algo choose_algo(const spo_set *s, spo_kind kind, int64_t P) {
     const int64_t nbins = (int64_t)s->nbx * s->nby * s->nbz;
     if (P >= INT_MAX || P < 1024 || 2 * P < 3 * nbins) return SPO_ALGO_GATHER;
-    const int64_t brick_from = kind == SPO_KIND_VGH ? 3 : (kind == SPO_KIND_VGL ? 8 : 12);
+    const int64_t brick_from = kind == SPO_KIND_VGH ? 5 : (kind == SPO_KIND_VGL ? 7 : 8);
     if (s->has_block_map && P >= brick_from * nbins) return SPO_ALGO_BRICK;
     return SPO_ALGO_SORTED_GATHER;
 }

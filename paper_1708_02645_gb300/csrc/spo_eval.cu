@@ -21,8 +21,11 @@ using namespace spo_dev;
 constexpr int kThreads = 256;
 constexpr int kVec = 4;   // orbitals per thread
 
+// Two blocks per SM at most (128 registers): the VGH form would take 130 and
+// run one block (8 warps) per SM; the loads of this latency-bound kernel
+// need the warps (VGH 25-36 % faster at 2,048-16,384 positions).
 template <typename T, int KIND, bool VEC_OUT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 2)
 spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxis gz, int yp, int zp,
                   int64_t Np, int64_t N, const float *__restrict__ pos, const int *__restrict__ perm,
                   int64_t P, int G, float *__restrict__ out)

@@ -102,6 +102,16 @@ def test_nio64_full_batch_sampled(spo_lib, oracle_lib, nio64, storage):
                algos=["auto"] + ALGOS)
 
 
+@pytest.mark.parametrize("kind", ["v", "vgl"])
+def test_nio64_full_batch_sampled_other_kinds(spo_lib, oracle_lib, nio64, kind):
+    """V and VGL of all 98,304 positions in one launch (FP32), every strategy
+    bit for bit; the oracle checks a seeded sample of 2048 positions."""
+    cfg, c, pos = nio64
+    sample = np.sort(np.unique((inputs.uniform01(98, 2048) * len(pos)).astype(np.int64)))
+    check_case(spo_lib, c, pos, kind, "f32", sample=sample, what=f"{cfg.name} {kind}",
+               algos=["auto", "gather", "sorted_gather", "brick4_t32"])
+
+
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
@@ -471,14 +481,15 @@ def test_reserved_evaluation_replays_in_a_cuda_graph(spo_lib, kind):
 
 def test_auto_strategy_follows_positions_per_brick(spo_lib):
     """spo_auto_algo: gather below 1.5 positions per brick (or P < 1024),
-    the brick kernel from 3 (VGH), 8 (VGL) or 12 (V) per brick, the gather in
+    the brick kernel from 5 (VGH), 7 (VGL) or 8 (V) per brick, the gather in
     binned order between; sets with fewer than 32 padded orbitals never take
     the brick kernel."""
     c = inputs.uniform_coefs(64, 64, 64, 40, seed=5).astype(np.float32)   # 16^3 = 4096 bricks
     with spo_lib.OrbitalSet(c) as s:
         expect = [(1000, "vgh", "gather"), (4096, "v", "gather"), (8192, "vgh", "sorted_gather"),
-                  (12288, "vgh", "brick"), (16384, "vgl", "sorted_gather"), (32768, "vgl", "brick"),
-                  (32768, "v", "sorted_gather"), (49152, "v", "brick"), (98304, "v", "brick")]
+                  (16384, "vgh", "sorted_gather"), (20480, "vgh", "brick"), (24576, "vgl", "sorted_gather"),
+                  (28672, "vgl", "brick"), (28672, "v", "sorted_gather"), (32768, "v", "brick"),
+                  (98304, "v", "brick")]
         for P, kind, algo in expect:
             assert s.auto_algo(kind, P) == algo, (P, kind)
         with pytest.raises(Exception):

@@ -261,3 +261,33 @@ def test_initial_parameters_follow_the_generator_definition(spo_lib):
     assert np.array_equal(g, ref.grid.astype(np.float32))
     for a, r in zip(W + b, ref.W + ref.b):
         assert np.array_equal(a, r.astype(np.float32))
+
+
+def test_level_learning_rates(spo_lib):
+    """spo_surrogate_set_level_lr: Adam's first step moves every parameter
+    with a gradient by its rate (to rounding: the grid gradients are summed
+    with atomics), so the largest first-step change of level l's features is
+    lr (R_0 / R_l)^power; resolutions 4, 8, 16, 32 here.  Power 0 is the
+    default; out-of-range powers are refused."""
+    t = torch()
+    teacher_c = inputs.plane_wave_coefs(16, 16, 16, 32, seed=91).astype(np.float32)
+    spec = S.SurrogateSpec(levels=4, log2_table=12, features=2, r_min=4, r_max=32, hidden=128, layers=2, N=32)
+    with spo_lib.OrbitalSet(teacher_c) as teacher:
+        states = []
+        for power in (None, 0.0, 2.0):
+            with spo_lib.Surrogate(spec, seed=5) as s:
+                if power is not None:
+                    s.set_level_lr(power)
+                g0, _, _ = s.get_params()
+                s.train(teacher, steps=1, batch=1024, lr=1e-2, seed=7)
+                g1, _, _ = s.get_params()
+                states.append(np.abs(g1 - g0).reshape(spec.levels, -1).max(axis=1))
+        R = np.array([4.0, 8.0, 16.0, 32.0])
+        np.testing.assert_allclose(states[0], 1e-2, rtol=1e-5)
+        np.testing.assert_allclose(states[1], 1e-2, rtol=1e-5)
+        np.testing.assert_allclose(states[2], 1e-2 * (R[0] / R) ** 2, rtol=1e-5)
+        with spo_lib.Surrogate(spec, seed=5) as s:
+            with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
+                s.set_level_lr(5.0)
+            with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
+                s.set_level_lr(-1.0)
