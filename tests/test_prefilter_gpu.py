@@ -6,7 +6,8 @@ Tolerances: FP64 data, 1e-12 of max |c| (two exact inversions of a
 well-conditioned operator, eigenvalues in [1/3, 1], differing only in
 rounding); FP32 data, 2e-6 of max |c| (the recursions keep FP64 state but
 read and write FP32 between passes); node values of an FP32 table, 1e-5 of
-max |f| (the FP32 kernel parity bound on V)."""
+max |f| (the FP32 kernel parity bound on V).  Shapes include a line of one
+node and a line of 400 nodes."""
 import numpy as np
 import pytest
 
@@ -21,7 +22,8 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("shape", [(4, 5, 6, 3), (16, 12, 20, 40), (48, 48, 48, 64), (3, 70, 1, 5)])
+@pytest.mark.parametrize("shape", [(4, 5, 6, 3), (16, 12, 20, 40), (48, 48, 48, 64), (3, 70, 1, 5),
+                                   (400, 3, 2, 2)])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_prefilter_matches_oracle(spo_lib, oracle_lib, shape, dtype):
     t = torch()
