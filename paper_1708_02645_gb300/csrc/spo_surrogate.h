@@ -33,9 +33,9 @@ struct SurrMlpView {
 // The fused kernel streams the weights from an image in global memory: one
 // block per hidden layer (128 rows in the 128-byte swizzle layout, one
 // K-block for the first layer, two for the others) and one per chunk of
-// kSurrOutChunk output rows (two K-blocks), in the order the kernel uses
-// them.
-constexpr int kSurrOutChunk = 96;
+// kSurrOutChunk output rows (two K-blocks of 128 rows, rows past the last
+// output zero), in the order the kernel uses them.
+constexpr int kSurrOutChunk = 128;
 constexpr int kSurrMaxLoads = 8;
 
 struct SurrImagePlan {

@@ -15,9 +15,12 @@
 //      columns 128..383;
 //   2. D_4 (Laplacian) into columns 0..127 from H[4]; the epilogue writes
 //      h_L = T + sp'(z0) z_L over H[4].
-// The output layer runs in chunks of 96 columns (5 x 96 <= 512), each chunk
-// storing FP32 [P][5][N] rows (bias on the value channel).  Value-only
-// evaluation carries channel 0 alone.
+// The output layer runs in chunks of 128 outputs with the operands swapped,
+// D_c[128 outputs x positions] = W_chunk H[c]^T (one output per tensor-memory
+// lane), the channels in rounds of as many as fit the 512 columns; a warp's
+// store then writes 32 consecutive outputs of one position (128 bytes)
+// instead of one 32-byte piece of 32 positions' rows.  Bias on the value
+// channel.  Value-only evaluation carries channel 0 alone.
 //
 // Weights do not stay resident (H takes 160 KB): one thread streams them
 // from an image pre-swizzled in global memory (one block per layer or output
@@ -46,7 +49,8 @@ using spo_detail::kSurrMaxLoads;
 constexpr int kThreads = 512;        // 16 warps: 4 per tensor-memory lane quarter
 constexpr int kTile = 128;           // positions per tile (MMA rows)
 constexpr int kHidden = 128;
-constexpr int kChunk = spo_detail::kSurrOutChunk;   // output columns per chunk
+constexpr int kChunk = spo_detail::kSurrOutChunk;   // outputs per chunk (MMA rows)
+static_assert(kChunk == 128, "an output chunk is one 128-row A operand");
 constexpr uint32_t kBlock = 128 * 128;              // K-block: 128 rows x 64 BF16
 constexpr uint32_t kChan = 2 * kBlock;              // one channel of H (K = 128)
 constexpr uint32_t kStage = 2 * kBlock;             // one weight stage
@@ -79,27 +83,29 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     return *reinterpret_cast<const uint32_t *>(&v);
 }
 
-// 8 floats (32 bytes, 32-byte aligned) streamed to global memory.
-__device__ __forceinline__ void store8_cs(float *p, const float *v) {
-    asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
-                 "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
-                 : "memory");
+// 1 / x by the hardware approximation (x in [1, 2] here: no special cases);
+// the activations it feeds are rounded to BF16.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
 
 __device__ __forceinline__ void softplus_jet(float z, float &sp, float &d1, float &d2) {
     const float e = __expf(-fabsf(z));
     sp = fmaxf(z, 0.0f) + __logf(1.0f + e);
-    const float r = __frcp_rn(1.0f + e);
+    const float r = rcp_approx(1.0f + e);
     d1 = z >= 0.0f ? r : e * r;
     d2 = d1 * (1.0f - d1);
 }
 
 // 8 BF16 (16 bytes) of row `row`, columns k .. k + 7 (k a multiple of 8) of
-// channel block ch.
-__device__ __forceinline__ void store_h8(uint8_t *H, int ch, int row, int k, const float (&h)[8]) {
-    uint8_t *blk = H + (uint32_t)ch * kChan + (uint32_t)(k >> 6) * kBlock;
-    *reinterpret_cast<uint4 *>(blk + sw128_offset(row, k & 63)) =
-        make_uint4(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]), pack_bf16(h[4], h[5]), pack_bf16(h[6], h[7]));
+// channel block ch of H (shared-memory address sH).
+__device__ __forceinline__ void store_h8(uint32_t sH, int ch, int row, int k, const float (&h)[8]) {
+    const uint32_t addr = sH + (uint32_t)ch * kChan + (uint32_t)(k >> 6) * kBlock + sw128_offset(row, k & 63);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(pack_bf16(h[0], h[1])),
+                 "r"(pack_bf16(h[2], h[3])), "r"(pack_bf16(h[4], h[5])), "r"(pack_bf16(h[6], h[7]))
+                 : "memory");
 }
 
 // Encoded features of every position, written as the shared-memory images
@@ -144,7 +150,6 @@ __global__ void encode_image_kernel(const __half2 *__restrict__ grid, SurrLevels
 __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __grid_constant__ FusedArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *H = sm;
     const uint32_t s0 = smem_addr(sm);
     const uint32_t sH = s0, sStage = s0 + kOffStage;
     const uint32_t full_bar = s0 + kOffBar;   // two barriers, 8 bytes apart
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
                             float d1, d2;
                             softplus_jet(z0[j] + bb[j], h[j], d1, d2);
                         }
-                        store_h8(H, 0, row, j0, h);
+                        store_h8(sH, 0, row, j0, h);
                     } else {
                         float zx[8], zy[8], zz[8];
                         tmem_ld8(lane_addr + 128u + (uint32_t)j0, zx);
@@ -284,10 +289,10 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
                             zy[j] *= d1v[j];
                             zz[j] *= d1v[j];
                         }
-                        store_h8(H, 0, row, j0, h0);
-                        store_h8(H, 1, row, j0, zx);
-                        store_h8(H, 2, row, j0, zy);
-                        store_h8(H, 3, row, j0, zz);
+                        store_h8(sH, 0, row, j0, h0);
+                        store_h8(sH, 1, row, j0, zx);
+                        store_h8(sH, 2, row, j0, zy);
+                        store_h8(sH, 3, row, j0, zz);
                         // park T and sp' in columns this thread has read (its own lane)
                         tmem_st8(lane_addr + 128u + (uint32_t)j0, t);
                         tmem_st8(lane_addr + 256u + (uint32_t)j0, d1v);
@@ -319,61 +324,76 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
                         tmem_ld8(lane_addr + 256u + (uint32_t)j0, d1v);
 #pragma unroll
                         for (int j = 0; j < 8; ++j) zl[j] = fmaf(d1v[j], zl[j], t[j]);
-                        store_h8(H, 4, row, j0, zl);
+                        store_h8(sH, 4, row, j0, zl);
                     }
                     fence_proxy_async_smem();
                     tc_fence_before_sync();
                     __syncthreads();
                 }
             } else {
-                // ---- output layer, chunks of kChunk columns
+                // ---- output layer: per chunk of 128 outputs, D_c[output][position]
+                // = W_chunk H[c]^T, N = the tile's positions rounded up to 16
                 const float *bias = a.b[l];
-                const int64_t p = row < a.tile_pos ? tile * a.tile_pos + row : a.P;
-                for (int n0 = 0, ci = 0; n0 < a.N; n0 += kChunk, ++ci) {
-                    const int nn = min(kChunk, a.N - n0);
+                const int np16 = (a.tile_pos + 15) & ~15;
+                const int cpr = min(a.nch, (int)kTmemCols / np16);   // channels per round
+                const int64_t p0 = tile * a.tile_pos;
+                const int npos = (int)min((int64_t)a.tile_pos, a.P - p0);
+                const int subs = (npos + 15) / 16;
+                for (int n0 = 0, ci = 0; n0 < a.N && !failed; n0 += kChunk, ++ci) {
                     const uint64_t g = (uint64_t)it * (uint64_t)a.nloads + (uint64_t)(l + ci);
                     const uint32_t stage = sStage + (uint32_t)(g & 1) * kStage;
-                    bool bad = false;
-                    if (leader) {
-                        tc_fence_after_sync();
-                        bad = !weights_ready(g);
-                        if (!bad) {
-                            for (int c = 0; c < a.nch; ++c)
-                                for (int kk = 0; kk < kHidden / 16; ++kk) {
-                                    const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
-                                    umma_bf16(tmem + (uint32_t)(kChunk * c),
-                                              umma_desc_sw128(sH + c * kChan + kb * kBlock + ko),
-                                              umma_desc_sw128(stage + kb * (uint32_t)nn * 128u + ko),
-                                              umma_idesc_bf16(128, nn), kk > 0);
-                                }
-                        }
-                        umma_commit(mma_bar);
-                    }
-                    if (!wait_mma(bad)) { failed = true; break; }
-                    if (leader) release(g);
-                    if (leader && n0 + kChunk >= a.N && tile + gridDim.x < ntiles) {
-                        // H is no longer read: bring in the next tile's features
-                        issue_features(tile + gridDim.x);
-                        feat_pending = true;
-                    }
-                    const int subs = nn / 16;
-                    for (int i = grp; i < a.nch * subs; i += 4) {
-                        const int c = i / subs, s = i - c * subs;
-                        float z[16];
-                        tmem_ld16(lane_addr + (uint32_t)(kChunk * c + 16 * s), z);
-                        if (p < a.P) {
-                            const int col = n0 + 16 * s;
-                            if (c == 0) {
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) z[j] += __ldg(bias + col + j);
+                    const int o = n0 + row;   // this thread's output: its tensor-memory lane
+                    const float bo = o < a.N ? __ldg(bias + o) : 0.0f;
+                    const int64_t step = (int64_t)a.nch * a.N;       // one position in out
+                    float *const obase = a.out + p0 * step + o;      // position p0, channel 0
+                    for (int c0 = 0; c0 < a.nch; c0 += cpr) {
+                        const int nc = min(cpr, a.nch - c0);
+                        bool bad = false;
+                        if (leader) {
+                            tc_fence_after_sync();
+                            if (c0 == 0) bad = !weights_ready(g);
+                            if (!bad) {
+                                for (int c = 0; c < nc; ++c)
+                                    for (int kk = 0; kk < kHidden / 16; ++kk) {
+                                        const uint32_t kb = kk >> 2, ko = (kk & 3) * 32;
+                                        umma_bf16(tmem + (uint32_t)(np16 * c),
+                                                  umma_desc_sw128(stage + kb * kBlock + ko),
+                                                  umma_desc_sw128(sH + (c0 + c) * kChan + kb * kBlock + ko),
+                                                  umma_idesc_bf16(128, np16), kk > 0);
+                                    }
                             }
-                            float *dst = a.nch == 1 ? a.out + p * a.N + col : a.out + (p * 5 + c) * a.N + col;
-                            store8_cs(dst, z);
-                            store8_cs(dst + 8, z + 8);
+                            umma_commit(mma_bar);
                         }
+                        if (!wait_mma(bad)) { failed = true; break; }
+                        if (c0 + nc >= a.nch) {
+                            if (leader) release(g);
+                            if (leader && n0 + kChunk >= a.N && tile + gridDim.x < ntiles) {
+                                // H is no longer read: bring in the next tile's features
+                                issue_features(tile + gridDim.x);
+                                feat_pending = true;
+                            }
+                        }
+                        for (int i = grp; i < nc * subs; i += 4) {
+                            const int c = i / subs, s = i - c * subs;
+                            float z[16];
+                            tmem_ld16(lane_addr + (uint32_t)(np16 * c + 16 * s), z);
+                            if (o < a.N) {
+                                const float add = c0 + c == 0 ? bo : 0.0f;
+                                float *dst = obase + (int64_t)(16 * s) * step + (int64_t)(c0 + c) * a.N;
+                                if (16 * s + 16 <= npos) {   // a full group of 16 positions
+#pragma unroll
+                                    for (int j = 0; j < 16; ++j, dst += step) __stcs(dst, z[j] + add);
+                                } else {
+                                    const int jn = npos - 16 * s;
+#pragma unroll
+                                    for (int j = 0; j < 16; ++j, dst += step)
+                                        if (j < jn) __stcs(dst, z[j] + add);
+                                }
+                            }
+                        }
+                        tc_fence_before_sync();
+                        __syncthreads();
                     }
-                    tc_fence_before_sync();
-                    __syncthreads();
                 }
             }
         }
@@ -398,12 +418,14 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
 
 // Writes the weight image: load 0 = W0 ([128][K0], one K-block, columns
 // K0..63 zero), loads 1 .. nl-2 = hidden matrices (two K-blocks), then the
-// output matrix in chunks of kChunk rows (two K-blocks of nn rows each).
+// output matrix in chunks of kChunk rows (two K-blocks of 128 rows each,
+// rows past the last output zero).
 // One thread per 16-byte chunk of a block.
 struct ImageArgs {
     const __nv_bfloat16 *W[spo_detail::kSurrMaxMats];
     uint32_t load_off[kSurrMaxLoads];
     int load_layer[kSurrMaxLoads], load_row0[kSurrMaxLoads], load_rows[kSurrMaxLoads], load_kblocks[kSurrMaxLoads];
+    int load_valid[kSurrMaxLoads];   // rows taken from W; the rest are zero
     int in_width[kSurrMaxLoads];
     int nloads;
 };
@@ -411,6 +433,7 @@ struct ImageArgs {
 __global__ void weight_image_kernel(const __grid_constant__ ImageArgs ia, uint8_t *img) {
     for (int i = 0; i < ia.nloads; ++i) {
         const int rows = ia.load_rows[i], kbs = ia.load_kblocks[i], in = ia.in_width[i];
+        const int valid = ia.load_valid[i];
         const __nv_bfloat16 *W = ia.W[ia.load_layer[i]];
         const int n = rows * kbs * 8;   // 16-byte chunks
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
@@ -418,7 +441,7 @@ __global__ void weight_image_kernel(const __grid_constant__ ImageArgs ia, uint8_
             const int r = rem / 8, kc = rem - r * 8;
             const int k = kb * 64 + kc * 8;
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (k < in) v = *reinterpret_cast<const uint4 *>(W + (size_t)(ia.load_row0[i] + r) * in + k);
+            if (k < in && r < valid) v = *reinterpret_cast<const uint4 *>(W + (size_t)(ia.load_row0[i] + r) * in + k);
             *reinterpret_cast<uint4 *>(img + ia.load_off[i] + (uint32_t)kb * (uint32_t)rows * 128u +
                                        sw128_offset(r, kc * 8)) = v;
         }
@@ -449,9 +472,8 @@ SurrImagePlan surrogate_image_plan(const SurrMlpView &v) {
     }
     const int N = v.widths[v.nl];
     for (int n0 = 0; n0 < N; n0 += kChunk) {
-        const int nn = std::min(kChunk, N - n0);
         plan.off[n] = off;
-        plan.bytes[n] = 2u * (uint32_t)nn * 128u;
+        plan.bytes[n] = 2u * kBlock;   // a full 128-row A operand
         off += plan.bytes[n++];
     }
     plan.nloads = n;
@@ -469,6 +491,7 @@ cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &pla
         ia.load_layer[n] = l;
         ia.load_row0[n] = 0;
         ia.load_rows[n] = kHidden;
+        ia.load_valid[n] = kHidden;
         ia.load_kblocks[n] = l == 0 ? 1 : 2;
         ia.in_width[n] = v.widths[l];
     }
@@ -477,7 +500,8 @@ cudaError_t surrogate_write_image(const SurrMlpView &v, const SurrImagePlan &pla
         ia.load_off[n] = plan.off[n];
         ia.load_layer[n] = v.nl - 1;
         ia.load_row0[n] = n0;
-        ia.load_rows[n] = std::min(kChunk, N - n0);
+        ia.load_rows[n] = kChunk;
+        ia.load_valid[n] = std::min(kChunk, N - n0);
         ia.load_kblocks[n] = 2;
         ia.in_width[n] = kHidden;
     }
