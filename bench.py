@@ -577,7 +577,7 @@ def run_ours(args):
 
 
 VARIANTS = ("all", "storage", "ratio", "nlpp", "autotune", "crowd", "surrogate", "surrogate_specified",
-            "prefilter", "nio32")
+            "surrogate_inference", "prefilter", "nio32")
 
 
 def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo, oracle_sample=None):
@@ -630,6 +630,8 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo, o
         res["crowd"] = measure_crowd(args, kind, steps)
     if cfg.N == 384 and (want("surrogate") or "surrogate_specified" in chosen):
         res["surrogate"] = measure_surrogate(cfg, s32, pos, steps, coarse_run=want("surrogate"))
+    if cfg.N == 384 and "surrogate_inference" in chosen:
+        res["surrogate_inference"] = measure_surrogate_inference(cfg, pos, steps)
     if want("prefilter"):
         res["prefilter"] = measure_prefilter(cfg)
     if want("nio32"):
@@ -732,6 +734,52 @@ def measure_prefilter(cfg):
                     "(3 axis passes, each reading and writing the table at least once)"}
 
 
+def time_surrogate_inference(sg, pos, N, steps):
+    """CUDA-event time of the fused tensor-core inference (VGL and V) of
+    surrogate sg at positions pos, after 3 untimed calls."""
+    import torch
+    P = pos.shape[0]
+    res = {}
+    out = torch.empty((P, 5, N), dtype=torch.float32, device=pos.device)
+    outv = torch.empty((P, N), dtype=torch.float32, device=pos.device)
+    for kd, o in (("vgl", out), ("v", outv)):
+        for _ in range(3):
+            sg.eval(pos, out=o, kind=kd, precision=1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            sg.eval(pos, out=o, kind=kd, precision=1)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        res[f"inference_{kd}"] = {"value": P * N / (ms * 1e-3), "unit": "evals/s",
+                                  "ms_per_step": round(ms, 5),
+                                  "kernels": "encode_image_kernel + surrogate_fused_kernel "
+                                             "(tcgen05, BF16 x BF16 -> FP32)"}
+    return res
+
+
+def surrogate_spec(N, r_min=2, r_max=64):
+    """The specified surrogate: 16 levels x 2^19 x 2 FP16 hashed grid,
+    32-128-128-128-N BF16 perceptron."""
+    from types import SimpleNamespace
+    return SimpleNamespace(levels=16, log2_table=19, features=2, r_min=r_min, r_max=r_max, hidden=128,
+                           layers=3, N=N)
+
+
+def measure_surrogate_inference(cfg, pos, steps):
+    """Inference time of the specified surrogate, untrained (its weights'
+    values do not change the work): the short command the inference kernel
+    is profiled with."""
+    from paper_1708_02645_gb300 import spo
+    spec = surrogate_spec(cfg.N)
+    with spo.Surrogate(spec, seed=20170808) as sg:
+        res = {"spec": vars(spec), "weights": "initial (untrained)"}
+        res.update(time_surrogate_inference(sg, pos, cfg.N, steps))
+    return res
+
+
 def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_lr_mult=10.0):
     """Train one surrogate on spline VGL samples with the variance-normalised
     V, G, L loss (channel weights 1 / mean(target_c^2) over 16,384 uniform
@@ -769,23 +817,8 @@ def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_
         res["train_samples"] = train_steps * batch
         res["train_s"] = round(time.perf_counter() - t0, 3)
         res["final_loss"] = loss
+        res.update(time_surrogate_inference(sg, pos, N, steps))
         out = torch.empty((P, 5, N), dtype=torch.float32, device=pos.device)
-        outv = torch.empty((P, N), dtype=torch.float32, device=pos.device)
-        for kd, o in (("vgl", out), ("v", outv)):
-            for _ in range(3):
-                sg.eval(pos, out=o, kind=kd, precision=1)
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(steps):
-                sg.eval(pos, out=o, kind=kd, precision=1)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
-            res[f"inference_{kd}"] = {"value": P * N / (ms * 1e-3), "unit": "evals/s",
-                                      "ms_per_step": round(ms, 5),
-                                      "kernels": "encode_image_kernel + surrogate_fused_kernel "
-                                                 "(tcgen05, BF16 x BF16 -> FP32)"}
         sg.eval(pos, out=out, kind="vgl", precision=1)
         want = torch.empty_like(out)
         teacher.eval(pos, "vgl", out=want)
@@ -816,18 +849,15 @@ def measure_surrogate(cfg, teacher, pos, steps, coarse_run=True):
     finest at the spline's own 64^3 grid; the reading this network is
     reported on) and, for comparison, 16..512 (the hashed-grid default,
     whose finest levels keep the Laplacian term from training)."""
-    from types import SimpleNamespace
     res = {"loss": "sum over V, Gx, Gy, Gz, L of w_c mean squared error, w_c = 1 / mean(target_c^2)",
            "rank_floor_what": "relative RMS error of the best rank-(hidden + 1) approximation of "
                               "the [8192 positions x N] matrix of spline values: a lower bound for "
                               "any output layer reading the hidden units"}
-    spec = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=2, r_max=64, hidden=128,
-                           layers=3, N=cfg.N)
+    spec = surrogate_spec(cfg.N)
     res["specified"] = surrogate_run(spec, teacher, pos, steps, 1.5e-2, 8192, 512, 128)
     if not coarse_run:
         return res
-    fine = SimpleNamespace(levels=16, log2_table=19, features=2, r_min=16, r_max=512, hidden=128,
-                           layers=3, N=cfg.N)
+    fine = surrogate_spec(cfg.N, 16, 512)
     res["resolutions_16_512"] = surrogate_run(fine, teacher, pos, steps, 1.5e-2, 8192, 512, 128)
     return res
 
@@ -949,7 +979,8 @@ def main(argv=None):
     ap.add_argument("--variants", default="all",
                     help="comma list of the sub-results to measure: storage, ratio, autotune, crowd, "
                          "surrogate (both networks), surrogate_specified (the specified network "
-                         "only), prefilter, nio32 (default all)")
+                         "only), surrogate_inference (the specified network untrained, inference "
+                         "timing only; not part of all), prefilter, nio32 (default all)")
     ap.add_argument("--positions", type=int, default=0,
                     help="evaluate this many positions instead of the workload's (profiling)")
     args = ap.parse_args(argv)
