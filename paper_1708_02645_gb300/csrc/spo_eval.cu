@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "spo_device.cuh"
+#include "spo_index.cuh"
 #include "spo_internal.h"
 
 namespace {
@@ -33,8 +34,8 @@ spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxi
     constexpr int NC = Rows<KIND>::value;
     const int64_t item = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (item >= P * G) return;
-    const int64_t i = item / G;
-    const int q = (int)(item - i * G);
+    int q;
+    const int64_t i = div_index(item, G, q);
     const int64_t p = perm ? (int64_t)__ldg(perm + i) : i;
 
     XAxis X;

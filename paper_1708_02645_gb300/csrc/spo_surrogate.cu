@@ -39,6 +39,7 @@ using spo_detail::DeviceGuard;
 using spo_detail::fail;
 using spo_detail::SurrLevels;
 using spo_dev::level_corners;
+using spo_dev::div_index;
 
 constexpr int kMaxLayers = 8;   // weight matrices (hidden layers + output)
 
@@ -60,8 +61,8 @@ __global__ void encode_fwd_kernel(const TG *__restrict__ grid, SurrLevels lv, co
     const int W = L * F;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = it / L;
-        const int l = (int)(it - p * L);
+        int l;
+        const int64_t p = div_index(it, L, l);
         float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
         uint32_t slot[8];
         float cw[5][8];
@@ -88,8 +89,8 @@ __global__ void encode_bwd_kernel(SurrLevels lv, const float *__restrict__ pos, 
     const int W = L * F;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = it / L;
-        const int l = (int)(it - p * L);
+        int l;
+        const int64_t p = div_index(it, L, l);
         float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
         uint32_t slot[8];
         float cw[5][8];
@@ -341,8 +342,8 @@ __device__ __forceinline__ void act_bwd_one(const float *zp, const float *gp, in
 __global__ void act_fwd_kernel(const float *__restrict__ z, float *__restrict__ h, int64_t P, int W) {
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * W;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = it / W;
-        const int j = (int)(it - p * W);
+        int j;
+        const int64_t p = div_index(it, W, j);
         float o[5];
         act_fwd_one(z + p * 5 * W + j, W, o);
         float *hp = h + p * 5 * W + j;
@@ -355,8 +356,8 @@ __global__ void act_bwd_kernel(const float *__restrict__ z, const float *__restr
                                float *__restrict__ gz, int64_t P, int W) {
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * W;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = it / W;
-        const int j = (int)(it - p * W);
+        int j;
+        const int64_t p = div_index(it, W, j);
         float o[5];
         act_bwd_one(z + p * 5 * W + j, g + p * 5 * W + j, W, o);
         float *op = gz + p * 5 * W + j;

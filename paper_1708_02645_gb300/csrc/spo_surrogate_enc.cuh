@@ -7,6 +7,8 @@
 
 #include <stdint.h>
 
+#include "spo_index.cuh"
+
 namespace spo_dev {
 
 __device__ __forceinline__ void smooth_w(float t, float &s, float &ds, float &d2s) {

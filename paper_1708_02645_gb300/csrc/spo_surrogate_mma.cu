@@ -119,10 +119,9 @@ __global__ void encode_image_kernel(const __half2 *__restrict__ grid, SurrLevels
     const int L = lv.levels;
     for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < P * L;
          it += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = it / L;
-        const int l = (int)(it - p * L);
-        const int64_t tile = p / tile_pos;
-        const int row = (int)(p - tile * tile_pos);
+        int l, row;
+        const int64_t p = div_index(it, L, l);
+        const int64_t tile = div_index(p, tile_pos, row);
         const float r[3] = {__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2)};
         uint32_t slot[8];
         float cw[5][8];
