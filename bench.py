@@ -780,10 +780,11 @@ def measure_surrogate_inference(cfg, pos, steps):
     return res
 
 
-def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_lr_mult=10.0):
+def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_lr_mult=10.0,
+                  channel_scale=(1.0, 1.0, 1.0, 1.0, 1.0), seed=20170808):
     """Train one surrogate on spline VGL samples with the variance-normalised
-    V, G, L loss (channel weights 1 / mean(target_c^2) over 16,384 uniform
-    teacher samples), Adam with a linear warm-up over `warm` steps and a
+    V, G, L loss (channel weights channel_scale_c / mean(target_c^2) over
+    16,384 uniform teacher samples), Adam with a linear warm-up over `warm` steps and a
     cosine decay of the learning rate to 0 (stepped every 16 steps), then
     time its fused tensor-core inference (VGL and V) and measure its error
     against the spline and its footprint."""
@@ -798,10 +799,10 @@ def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_
                         "decay": "cosine to 0, the rate stepped every 16 steps"}}
     sp = torch.from_numpy(inputs.uniform_positions(16384, 20170810)).to(pos.device)
     t = teacher.eval(sp, "vgl").double()
-    cw = [float(1.0 / (t[:, c] ** 2).mean()) for c in range(5)]
+    cw = [float(channel_scale[c] / (t[:, c] ** 2).mean()) for c in range(5)]
     res["channel_weights"] = cw
     chunk = 16
-    with spo.Surrogate(spec, seed=20170808) as sg:
+    with spo.Surrogate(spec, seed=seed) as sg:
         sg.set_optimizer(0.9, 0.99, 1e-15, grid_lr_mult)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -842,6 +843,12 @@ def surrogate_run(spec, teacher, pos, steps, lr, train_steps, batch, warm, grid_
     return res
 
 
+# Loss weight of each channel (V, Gx, Gy, Gz, L) relative to 1 / mean(target^2):
+# the value enters every determinant ratio, the derivatives only the drift
+# and the local energy, so it counts twice.
+SURROGATE_CHANNEL_SCALE = (2.0, 1.0, 1.0, 1.0, 1.0)
+
+
 def measure_surrogate(cfg, teacher, pos, steps, coarse_run=True):
     """Learned surrogates of the 384-orbital set, both with the specified
     capacity (16 levels x 2^19 x 2 FP16 hashed grid, 32-128-128-128-384 BF16
@@ -849,16 +856,19 @@ def measure_surrogate(cfg, teacher, pos, steps, coarse_run=True):
     finest at the spline's own 64^3 grid; the reading this network is
     reported on) and, for comparison, 16..512 (the hashed-grid default,
     whose finest levels keep the Laplacian term from training)."""
-    res = {"loss": "sum over V, Gx, Gy, Gz, L of w_c mean squared error, w_c = 1 / mean(target_c^2)",
+    res = {"loss": "sum over V, Gx, Gy, Gz, L of w_c mean squared error, w_c = s_c / mean(target_c^2), "
+                   "s = (2, 1, 1, 1, 1): the value counted twice",
            "rank_floor_what": "relative RMS error of the best rank-(hidden + 1) approximation of "
                               "the [8192 positions x N] matrix of spline values: a lower bound for "
                               "any output layer reading the hidden units"}
     spec = surrogate_spec(cfg.N)
-    res["specified"] = surrogate_run(spec, teacher, pos, steps, 1.5e-2, 8192, 512, 128)
+    res["specified"] = surrogate_run(spec, teacher, pos, steps, 1.5e-2, 8192, 512, 128,
+                                     channel_scale=SURROGATE_CHANNEL_SCALE)
     if not coarse_run:
         return res
     fine = surrogate_spec(cfg.N, 16, 512)
-    res["resolutions_16_512"] = surrogate_run(fine, teacher, pos, steps, 1.5e-2, 8192, 512, 128)
+    res["resolutions_16_512"] = surrogate_run(fine, teacher, pos, steps, 1.5e-2, 8192, 512, 128,
+                                              channel_scale=SURROGATE_CHANNEL_SCALE)
     return res
 
 
