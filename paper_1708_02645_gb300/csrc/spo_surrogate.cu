@@ -612,11 +612,59 @@ __device__ __forceinline__ void adam_one(float &p, float &g, float &m, float &v,
     g = 0.0f;
 }
 
+// Device-side state of a training call: the learning rate, Adam's step
+// count and bias corrections, and the index of the current step within the
+// run of samples drawn together.  Kept on the device so that one captured
+// step (a CUDA graph) serves every step of the call.
+struct TrainState {
+    double t;     // Adam steps taken
+    float lr;     // the call's learning rate
+    float c1, c2; // 1 - beta1^t, 1 - beta2^t
+    int64_t k;    // step within the current run of samples
+};
+
+__global__ void train_begin_kernel(TrainState *ts, float lr, int64_t t) {
+    ts->lr = lr;
+    ts->t = (double)t;
+    ts->k = 0;
+}
+
+// Copies the samples and spline values of step k of the run into the
+// step's fixed buffers.
+__global__ void stage_step_kernel(const TrainState *__restrict__ ts, const float *__restrict__ tpos,
+                                  const float *__restrict__ ttarget, int64_t npos, int64_t ntgt,
+                                  float *__restrict__ pos, float *__restrict__ target) {
+    const int64_t k = ts->k;
+    const float *sp = tpos + k * npos, *sg = ttarget + k * ntgt;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x, i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = ntgt % 4 == 0 && ((reinterpret_cast<uintptr_t>(sg) | reinterpret_cast<uintptr_t>(target)) & 15u) == 0;
+    if (vec) {
+        for (int64_t i = i0; i < ntgt / 4; i += stride)
+            reinterpret_cast<float4 *>(target)[i] = reinterpret_cast<const float4 *>(sg)[i];
+    } else {
+        for (int64_t i = i0; i < ntgt; i += stride) target[i] = sg[i];
+    }
+    for (int64_t i = i0; i < npos; i += stride) pos[i] = sp[i];
+}
+
+// The next step: Adam's step count and bias corrections (in double, rounded
+// once to float), and the next sample index.
+__global__ void train_tick_kernel(TrainState *ts, float b1, float b2) {
+    const double t = ts->t + 1.0;
+    ts->t = t;
+    ts->c1 = (float)(1.0 - pow((double)b1, t));
+    ts->c2 = (float)(1.0 - pow((double)b2, t));
+    ts->k += 1;
+}
+
 // One Adam step over n parameters (the gradient is zeroed for the next
-// step); four per thread when the arrays are 16-byte aligned.
+// step); four per thread when the arrays are 16-byte aligned.  The rate is
+// (the call's rate x lr_mult) x lr_scale, the bias corrections those of the
+// step state.
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
-                            float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
-                            float c1, float c2) {
+                            float *__restrict__ v, int64_t n, const TrainState *__restrict__ ts, float lr_mult,
+                            float lr_scale, float b1, float b2, float eps) {
+    const float lr = ts->lr * lr_mult * lr_scale, c1 = ts->c1, c2 = ts->c2;
     const bool vec = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
                        reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15u) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
@@ -638,7 +686,11 @@ __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float 
 }
 
 // uniform positions in the unit cube, splitmix64 on (seed, counter)
-__global__ void sample_kernel(float *pos, int64_t n3, unsigned long long seed, unsigned long long base) {
+// Uniform samples of a run of steps; also restarts the step state's sample
+// index.
+__global__ void sample_kernel(float *pos, int64_t n3, unsigned long long seed, unsigned long long base,
+                              TrainState *ts) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ts->k = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
          i += (int64_t)gridDim.x * blockDim.x) {
         unsigned long long z = seed + (base + (unsigned long long)i + 1ull) * 0x9E3779B97F4A7C15ull;
@@ -735,6 +787,14 @@ struct spo_surrogate {
     // evaluated together (grown)
     float *tpos = nullptr, *ttarget = nullptr;
     int64_t tcap = 0;
+
+    // one training step captured as a CUDA graph, replayed for every step
+    // whose inputs (sizes, buffers, settings: step_key) match the capture
+    TrainState *tstate = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t step_exec = nullptr;
+    std::vector<uint64_t> step_key;
+    bool graphs_off = false;   // a capture failed: steps run as plain launches
 };
 
 namespace {
@@ -1048,6 +1108,92 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
     return e;
 }
 
+// One training step over the batch of P samples: stage step k's samples,
+// forward, loss and backward, advance the step state, then Adam (the grid,
+// level by level when the levels take different rates, and the perceptron).
+cudaError_t enqueue_step(spo_surrogate *s, int64_t P, const ChannelWeights &cw, cudaStream_t st, bool tc) {
+    const int64_t npos = 3 * P, ntgt = 5 * P * s->spec.N;
+    stage_step_kernel<<<blocks_for(ntgt / 4 + 1), 256, 0, st>>>(s->tstate, s->tpos, s->ttarget, npos, ntgt,
+                                                                 s->pos, s->target);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st, tc);
+    if (e != cudaSuccess) return e;
+    train_tick_kernel<<<1, 1, 0, st>>>(s->tstate, s->beta1, s->beta2);
+    const float b1 = s->beta1, b2 = s->beta2;
+    if (s->level_lr_power == 0.0f) {
+        adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n, s->tstate,
+                                                           s->grid_lr_mult, 1.0f, b1, b2, s->eps);
+    } else {
+        const int64_t nlev = (int64_t)s->lv.table * s->lv.features;
+        for (int l = 0; l < s->lv.levels; ++l) {
+            const float scale = (float)std::pow((double)s->lv.R[0] / s->lv.R[l], (double)s->level_lr_power);
+            const int64_t o = l * nlev;
+            adam_kernel<<<blocks_for(nlev), 256, 0, st>>>(s->param + o, s->grad + o, s->m1 + o, s->m2 + o, nlev,
+                                                          s->tstate, s->grid_lr_mult, scale, b1, b2, s->eps);
+        }
+    }
+    const int64_t nm = s->nparam - s->grid_n;
+    adam_kernel<<<blocks_for(nm), 256, 0, st>>>(s->param + s->grid_n, s->grad + s->grid_n, s->m1 + s->grid_n,
+                                                s->m2 + s->grid_n, nm, s->tstate, 1.0f, 1.0f, b1, b2, s->eps);
+    return cudaGetLastError();
+}
+
+// Everything a captured step depends on: sizes, settings and the buffers
+// its launches name.  A different key means a new capture.
+std::vector<uint64_t> step_key(const spo_surrogate *s, int64_t P, const ChannelWeights &cw, bool tc) {
+    auto bits = [](float f) { uint32_t u; memcpy(&u, &f, 4); return (uint64_t)u; };
+    auto ptr = [](const void *p) { return (uint64_t)reinterpret_cast<uintptr_t>(p); };
+    std::vector<uint64_t> k = {(uint64_t)P, (uint64_t)tc, bits(s->beta1), bits(s->beta2), bits(s->eps),
+                               bits(s->grid_lr_mult), bits(s->level_lr_power), (uint64_t)s->img_M,
+                               ptr(s->pos), ptr(s->target), ptr(s->tpos), ptr(s->ttarget), ptr(s->tstate),
+                               ptr(s->param), ptr(s->grad), ptr(s->m1), ptr(s->m2), ptr(s->dacc), ptr(s->img),
+                               ptr(s->ia), ptr(s->ib), ptr(s->gbuf[0]), ptr(s->gbuf[1])};
+    for (int c = 0; c < 5; ++c) k.push_back(bits(cw.w[c]));
+    for (int l = 0; l <= s->nl; ++l) k.push_back(ptr(s->act[l]));
+    for (int l = 0; l < s->nl; ++l) {
+        k.push_back(ptr(s->pre[l]));
+        k.push_back(ptr(s->xt[l]));
+        k.push_back(ptr(s->wd[l]));
+        k.push_back(ptr(s->wt[l]));
+    }
+    return k;
+}
+
+// Runs one training step: a replay of the captured step when it matches
+// (capturing it first when it does not), plain launches when capture is
+// not possible.
+cudaError_t run_step(spo_surrogate *s, int64_t P, const ChannelWeights &cw, cudaStream_t st, bool tc,
+                     bool replay) {
+    if (!replay || s->graphs_off) return enqueue_step(s, P, cw, st, tc);
+    std::vector<uint64_t> key = step_key(s, P, cw, tc);
+    if (!s->step_exec || key != s->step_key) {
+        if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+        s->step_exec = nullptr;
+        if (!s->cap_stream && cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s->graphs_off = true;
+            return enqueue_step(s, P, cw, st, tc);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t eq = enqueue_step(s, P, cw, s->cap_stream, tc);
+            e = cudaStreamEndCapture(s->cap_stream, &g);
+            if (e == cudaSuccess) e = eq;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->step_exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {   // not capturable here: plain launches from now on
+            cudaGetLastError();
+            s->step_exec = nullptr;
+            s->graphs_off = true;
+            return enqueue_step(s, P, cw, st, tc);
+        }
+        s->step_key = std::move(key);
+    }
+    return cudaGraphLaunch(s->step_exec, st);
+}
+
 
 
 }  // namespace
@@ -1183,6 +1329,9 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     cudaFree(s->grid16); cudaFree(s->w16); cudaFree(s->dacc); cudaFree(s->wimg);
     cudaFree(s->feat);
     cudaFree(s->img);
+    cudaFree(s->tstate);
+    if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
     return SPO_OK;
 }
@@ -1326,15 +1475,21 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
     run = std::max<int64_t>(1, std::min<int64_t>(run, steps));
     rs = grow_teacher(s, run * P);
     if (rs != SPO_OK) return rs;
+    if (!s->tstate && cudaMalloc(&s->tstate, sizeof(TrainState)) != cudaSuccess) {
+        cudaGetLastError();
+        s->tstate = nullptr;
+        return fail(SPO_ENOMEM, "training step state");
+    }
     ChannelWeights cw{};
     double loss_h = 0.0;
-    cudaError_t e = cudaSuccess;
+    train_begin_kernel<<<1, 1, 0, st>>>(s->tstate, lr, s->adam_t);
+    cudaError_t e = cudaGetLastError();
     for (int64_t step = 0; step < steps && e == cudaSuccess; ++step) {
         const int64_t k = step % run;
-        if (k == 0) {
+        if (k == 0) {   // the next run's samples and their spline values (restarts the sample index)
             const int64_t n = std::min<int64_t>(run, steps - step) * P;
             sample_kernel<<<blocks_for(3 * n), 256, 0, st>>>(s->tpos, 3 * n, seed,
-                                                               (unsigned long long)step * 3 * P);
+                                                               (unsigned long long)step * 3 * P, s->tstate);
             const spo_status es = spo_detail::eval_queue(teacher, SPO_KIND_VGL, s->tpos, n, s->ttarget, st,
                                                          SPO_ALGO_AUTO);
             if (es != SPO_OK) {   // keep the inference copies in step with the parameters taken so far
@@ -1343,36 +1498,12 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
                 return es;
             }
         }
-        const float *pos = s->tpos + 3 * k * P;
-        const float *target = s->ttarget + 5 * k * P * s->spec.N;
-        if (step == 0) e = channel_weights_for(s, target, P, channel_weights, cw, st);
-        if (e == cudaSuccess) e = backward(s, pos, target, P, cw, st, s->train_precision == 1);
-        if (e == cudaSuccess) {
-            ++s->adam_t;
-            const float b1 = s->beta1, b2 = s->beta2;
-            const float c1 = (float)(1.0 - std::pow((double)b1, (double)s->adam_t));
-            const float c2 = (float)(1.0 - std::pow((double)b2, (double)s->adam_t));
-            // the grid (the first grid_n parameters, level by level) and the
-            // perceptron may take different rates
-            if (s->level_lr_power == 0.0f) {
-                adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n,
-                                                                   lr * s->grid_lr_mult, b1, b2, s->eps, c1, c2);
-            } else {
-                const int64_t nlev = (int64_t)s->lv.table * s->lv.features;
-                for (int l = 0; l < s->lv.levels; ++l) {
-                    const float scale = (float)std::pow((double)s->lv.R[0] / s->lv.R[l], (double)s->level_lr_power);
-                    const int64_t o = l * nlev;
-                    adam_kernel<<<blocks_for(nlev), 256, 0, st>>>(s->param + o, s->grad + o, s->m1 + o, s->m2 + o,
-                                                                  nlev, lr * s->grid_lr_mult * scale, b1, b2,
-                                                                  s->eps, c1, c2);
-                }
-            }
-            const int64_t nm = s->nparam - s->grid_n;
-            adam_kernel<<<blocks_for(nm), 256, 0, st>>>(s->param + s->grid_n, s->grad + s->grid_n,
-                                                        s->m1 + s->grid_n, s->m2 + s->grid_n, nm, lr, b1, b2,
-                                                        s->eps, c1, c2);
-            e = cudaGetLastError();
-        }
+        if (step == 0)
+            e = channel_weights_for(s, s->ttarget, P, channel_weights, cw, st);
+        // the first step of a call runs as plain launches (it grows the
+        // scratch the captured step then names); the others replay it
+        if (e == cudaSuccess) e = run_step(s, P, cw, st, s->train_precision == 1, step > 0);
+        if (e == cudaSuccess) ++s->adam_t;
         if (e == cudaSuccess && step == steps - 1) {
             e = cudaMemcpyAsync(&loss_h, s->dacc, sizeof(double), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
