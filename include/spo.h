@@ -360,13 +360,17 @@ spo_status spo_prefilter(const spo_grid *grid, int64_t N, void *data, spo_dtype 
  *   (coordinate i of step t: the top 24 bits of splitmix64(seed + (3 batch t
  *   + i + 1) 0x9E3779B97F4A7C15) over 2^24), evaluates the teacher's VGL
  *   for them (the spline kernels), and takes one Adam step on sum_c w_c
- *   mean((out_c - target_c)^2).  channel_weights = 5 floats (V, Gx, Gy, Gz,
+ *   mean((out_c - target_c)^2): dense for the perceptron, sparse for the
+ *   grid (an entry with no gradient in the step keeps its value and both
+ *   moments).  channel_weights = 5 floats (V, Gx, Gy, Gz,
  *   L) or NULL for 1 / mean(target_c^2) of the first batch.  The teacher must
  *   have the same N.  The samples of several consecutive steps (enough for
  *   about 32 positions per brick of the teacher, at most 1 GiB of teacher
  *   values) are drawn and evaluated in one launch and held on the device
- *   until used; the results equal step-by-step draws.  Synchronous;
- *   refreshes the inference copies.
+ *   until used; the results equal step-by-step draws.  The steps after a
+ *   call's first replay a CUDA graph of one step, captured when the sizes,
+ *   buffers or settings change.  Synchronous; refreshes the inference
+ *   copies.
  * spo_surrogate_eval(s, kind, pos, P, out, precision, stream): kind V or
  *   VGL; precision 0 evaluates the FP32 master parameters (CUDA cores),
  *   precision 1 the inference copies (FP16 grid, BF16 weights and

@@ -660,21 +660,29 @@ __global__ void train_tick_kernel(TrainState *ts, float b1, float b2) {
 // One Adam step over n parameters (the gradient is zeroed for the next
 // step); four per thread when the arrays are 16-byte aligned.  The rate is
 // (the call's rate x lr_mult) x lr_scale, the bias corrections those of the
-// step state.
+// step state.  lazy: a parameter whose gradient is zero in this step keeps
+// its value and both moments (the sparse form for the hash grid, whose
+// entries a batch touches only a few of), and a group of four such
+// parameters is not read past its gradients.
 __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float *__restrict__ m,
                             float *__restrict__ v, int64_t n, const TrainState *__restrict__ ts, float lr_mult,
-                            float lr_scale, float b1, float b2, float eps) {
+                            float lr_scale, float b1, float b2, float eps, int lazy) {
     const float lr = ts->lr * lr_mult * lr_scale, c1 = ts->c1, c2 = ts->c2;
     const bool vec = ((reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(g) |
                        reinterpret_cast<uintptr_t>(m) | reinterpret_cast<uintptr_t>(v)) & 15u) == 0;
     const int64_t n4 = vec ? n / 4 : 0;
+    auto step = [&](float &pp, float &gg, float &mm, float &vv) {
+        if (!lazy || gg != 0.0f) adam_one(pp, gg, mm, vv, lr, b1, b2, eps, c1, c2);
+    };
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-        float4 P4 = reinterpret_cast<float4 *>(p)[i], G4 = reinterpret_cast<float4 *>(g)[i];
+        float4 G4 = reinterpret_cast<float4 *>(g)[i];
+        if (lazy && G4.x == 0.0f && G4.y == 0.0f && G4.z == 0.0f && G4.w == 0.0f) continue;
+        float4 P4 = reinterpret_cast<float4 *>(p)[i];
         float4 M4 = reinterpret_cast<float4 *>(m)[i], V4 = reinterpret_cast<float4 *>(v)[i];
-        adam_one(P4.x, G4.x, M4.x, V4.x, lr, b1, b2, eps, c1, c2);
-        adam_one(P4.y, G4.y, M4.y, V4.y, lr, b1, b2, eps, c1, c2);
-        adam_one(P4.z, G4.z, M4.z, V4.z, lr, b1, b2, eps, c1, c2);
-        adam_one(P4.w, G4.w, M4.w, V4.w, lr, b1, b2, eps, c1, c2);
+        step(P4.x, G4.x, M4.x, V4.x);
+        step(P4.y, G4.y, M4.y, V4.y);
+        step(P4.z, G4.z, M4.z, V4.z);
+        step(P4.w, G4.w, M4.w, V4.w);
         reinterpret_cast<float4 *>(p)[i] = P4;
         reinterpret_cast<float4 *>(g)[i] = G4;
         reinterpret_cast<float4 *>(m)[i] = M4;
@@ -682,7 +690,7 @@ __global__ void adam_kernel(float *__restrict__ p, float *__restrict__ g, float 
     }
     for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
-        adam_one(p[i], g[i], m[i], v[i], lr, b1, b2, eps, c1, c2);
+        step(p[i], g[i], m[i], v[i]);
 }
 
 // uniform positions in the unit cube, splitmix64 on (seed, counter)
@@ -1110,7 +1118,8 @@ cudaError_t backward(spo_surrogate *s, const float *pos, const float *target, in
 
 // One training step over the batch of P samples: stage step k's samples,
 // forward, loss and backward, advance the step state, then Adam (the grid,
-// level by level when the levels take different rates, and the perceptron).
+// level by level when the levels take different rates, sparse: only the
+// entries the batch touched; and the perceptron, dense).
 cudaError_t enqueue_step(spo_surrogate *s, int64_t P, const ChannelWeights &cw, cudaStream_t st, bool tc) {
     const int64_t npos = 3 * P, ntgt = 5 * P * s->spec.N;
     stage_step_kernel<<<blocks_for(ntgt / 4 + 1), 256, 0, st>>>(s->tstate, s->tpos, s->ttarget, npos, ntgt,
@@ -1122,19 +1131,19 @@ cudaError_t enqueue_step(spo_surrogate *s, int64_t P, const ChannelWeights &cw, 
     const float b1 = s->beta1, b2 = s->beta2;
     if (s->level_lr_power == 0.0f) {
         adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n, s->tstate,
-                                                           s->grid_lr_mult, 1.0f, b1, b2, s->eps);
+                                                           s->grid_lr_mult, 1.0f, b1, b2, s->eps, 1);
     } else {
         const int64_t nlev = (int64_t)s->lv.table * s->lv.features;
         for (int l = 0; l < s->lv.levels; ++l) {
             const float scale = (float)std::pow((double)s->lv.R[0] / s->lv.R[l], (double)s->level_lr_power);
             const int64_t o = l * nlev;
             adam_kernel<<<blocks_for(nlev), 256, 0, st>>>(s->param + o, s->grad + o, s->m1 + o, s->m2 + o, nlev,
-                                                          s->tstate, s->grid_lr_mult, scale, b1, b2, s->eps);
+                                                          s->tstate, s->grid_lr_mult, scale, b1, b2, s->eps, 1);
         }
     }
     const int64_t nm = s->nparam - s->grid_n;
     adam_kernel<<<blocks_for(nm), 256, 0, st>>>(s->param + s->grid_n, s->grad + s->grid_n, s->m1 + s->grid_n,
-                                                s->m2 + s->grid_n, nm, s->tstate, 1.0f, 1.0f, b1, b2, s->eps);
+                                                s->m2 + s->grid_n, nm, s->tstate, 1.0f, 1.0f, b1, b2, s->eps, 0);
     return cudaGetLastError();
 }
 
