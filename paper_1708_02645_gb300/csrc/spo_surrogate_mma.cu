@@ -144,6 +144,10 @@ __global__ void encode_image_kernel(const __half2 *__restrict__ grid, SurrLevels
                 *reinterpret_cast<uint32_t *>(base + (uint32_t)ch * kBlock + sw128_offset(row, 2 * l)) =
                     pack_bf16(acc[ch][0], acc[ch][1]);
     }
+    // the fused kernel may be scheduled once every block got here: the
+    // block triggers after all its threads' writes
+    __syncthreads();
+    grid_dependents_launch();
 }
 
 __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __grid_constant__ FusedArgs a) {
@@ -194,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) surrogate_fused_kernel(const __gr
     uint32_t feat_phase = 0;
     bool feat_pending = false;   // leader: a feature copy is in flight
     if (leader && blockIdx.x < ntiles) {
+        grid_dependency_wait();   // the encoding kernel's images are complete
         issue_features(blockIdx.x);
         feat_pending = true;
     }
@@ -560,8 +565,20 @@ cudaError_t surrogate_fused_tc(const SurrMlpView &v, const uint8_t *img, const S
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    surrogate_fused_kernel<<<grid_x, kThreads, kSmemBytes, stream>>>(a);
-    return cudaGetLastError();
+    // a programmatic dependent of the encoding: its set-up (tensor memory,
+    // barriers, the first weight copies) overlaps the encoding's last blocks,
+    // and the leader waits for the encoding before copying the first images
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr.val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid_x);
+    cfg.blockDim = dim3((unsigned)kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, surrogate_fused_kernel, a);
 }
 
 }  // namespace spo_detail
