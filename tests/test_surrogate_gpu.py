@@ -291,3 +291,48 @@ def test_level_learning_rates(spo_lib):
                 s.set_level_lr(5.0)
             with pytest.raises(spo_lib.SpoError, match="SPO_EINVAL"):
                 s.set_level_lr(-1.0)
+
+
+def _training_draw(seed, step, batch):
+    """Positions of step `step` of a training call, from the documented
+    stream: coordinate i is the top 24 bits of splitmix64(seed + (3 batch
+    step + i + 1) 0x9E3779B97F4A7C15) over 2^24."""
+    m64 = (1 << 64) - 1
+    out = np.empty(3 * batch, dtype=np.float32)
+    for i in range(3 * batch):
+        z = (seed + (3 * batch * step + i + 1) * 0x9E3779B97F4A7C15) & m64
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m64
+        z ^= z >> 31
+        out[i] = np.float32(z >> 40) / np.float32(16777216.0)
+    return out.reshape(batch, 3)
+
+
+def test_sparse_grid_updates_and_recapture(spo_lib):
+    """The grid's Adam step is sparse: in a training call, a grid entry moves
+    only if the call's batch gives it a gradient (dense Adam would also move
+    the entries only the previous call touched, whose first moment is not
+    zero); the perceptron's step is dense.  Calls that change the batch size
+    or the per-level rates between replays of the captured step keep
+    training, and the step count follows every step."""
+    t = torch()
+    coefs = inputs.plane_wave_coefs(12, 12, 12, 16, seed=41, kmax=2.0).astype(np.float32)
+    spec = S.SurrogateSpec(levels=4, log2_table=10, features=2, r_min=2, r_max=16, hidden=32, layers=1, N=16)
+    with spo_lib.OrbitalSet(coefs) as teacher, spo_lib.Surrogate(spec, seed=42) as s:
+        s.train(teacher, steps=1, batch=64, lr=1e-2, seed=43)
+        g1, W1, _ = s.get_params()
+        pos = t.from_numpy(_training_draw(44, 0, 64)).cuda()
+        _, gg, _, _ = s.grad(pos, teacher.eval(pos, kind="vgl"), precision=1)
+        s.train(teacher, steps=1, batch=64, lr=1e-2, seed=44)
+        g2, W2, _ = s.get_params()
+        moved, touched = g2 != g1, gg != 0
+        assert moved.any() and touched.sum() < 0.5 * touched.size
+        assert not (moved & ~touched).any(), int((moved & ~touched).sum())
+        for a, b in zip(W2, W1):
+            assert (a != b).mean() > 0.9
+        losses = [s.train(teacher, steps=4, batch=64, lr=1e-2, seed=45),
+                  s.train(teacher, steps=4, batch=128, lr=5e-3, seed=46)]
+        s.set_level_lr(1.0)
+        losses.append(s.train(teacher, steps=4, batch=128, lr=5e-3, seed=47))
+        assert np.all(np.isfinite(losses)), losses
+        assert s.state()[3] == 14
