@@ -617,15 +617,15 @@ __device__ __forceinline__ void adam_one(float &p, float &g, float &m, float &v,
 // run of samples drawn together.  Kept on the device so that one captured
 // step (a CUDA graph) serves every step of the call.
 struct TrainState {
-    double t;     // Adam steps taken
     float lr;     // the call's learning rate
-    float c1, c2; // 1 - beta1^t, 1 - beta2^t
+    float c1, c2; // 1 - beta1^t, 1 - beta2^t of the current step
+    int64_t j;    // step within the call
     int64_t k;    // step within the current run of samples
 };
 
-__global__ void train_begin_kernel(TrainState *ts, float lr, int64_t t) {
+__global__ void train_begin_kernel(TrainState *ts, float lr) {
     ts->lr = lr;
-    ts->t = (double)t;
+    ts->j = 0;
     ts->k = 0;
 }
 
@@ -647,13 +647,13 @@ __global__ void stage_step_kernel(const TrainState *__restrict__ ts, const float
     for (int64_t i = i0; i < npos; i += stride) pos[i] = sp[i];
 }
 
-// The next step: Adam's step count and bias corrections (in double, rounded
-// once to float), and the next sample index.
-__global__ void train_tick_kernel(TrainState *ts, float b1, float b2) {
-    const double t = ts->t + 1.0;
-    ts->t = t;
-    ts->c1 = (float)(1.0 - pow((double)b1, t));
-    ts->c2 = (float)(1.0 - pow((double)b2, t));
+// The next step: its bias corrections from the call's table (formed on the
+// host, in double, rounded once to float), and the next indices.
+__global__ void train_tick_kernel(TrainState *ts, const float2 *__restrict__ corr) {
+    const float2 c = corr[ts->j];
+    ts->c1 = c.x;
+    ts->c2 = c.y;
+    ts->j += 1;
     ts->k += 1;
 }
 
@@ -799,6 +799,8 @@ struct spo_surrogate {
     // one training step captured as a CUDA graph, replayed for every step
     // whose inputs (sizes, buffers, settings: step_key) match the capture
     TrainState *tstate = nullptr;
+    float2 *corr = nullptr;      // per step of a call: 1 - beta1^t, 1 - beta2^t
+    int64_t corr_cap = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t step_exec = nullptr;
     std::vector<uint64_t> step_key;
@@ -1127,7 +1129,7 @@ cudaError_t enqueue_step(spo_surrogate *s, int64_t P, const ChannelWeights &cw, 
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = backward(s, s->pos, s->target, P, cw, st, tc);
     if (e != cudaSuccess) return e;
-    train_tick_kernel<<<1, 1, 0, st>>>(s->tstate, s->beta1, s->beta2);
+    train_tick_kernel<<<1, 1, 0, st>>>(s->tstate, s->corr);
     const float b1 = s->beta1, b2 = s->beta2;
     if (s->level_lr_power == 0.0f) {
         adam_kernel<<<blocks_for(s->grid_n), 256, 0, st>>>(s->param, s->grad, s->m1, s->m2, s->grid_n, s->tstate,
@@ -1155,7 +1157,7 @@ std::vector<uint64_t> step_key(const spo_surrogate *s, int64_t P, const ChannelW
     std::vector<uint64_t> k = {(uint64_t)P, (uint64_t)tc, bits(s->beta1), bits(s->beta2), bits(s->eps),
                                bits(s->grid_lr_mult), bits(s->level_lr_power), (uint64_t)s->img_M,
                                ptr(s->pos), ptr(s->target), ptr(s->tpos), ptr(s->ttarget), ptr(s->tstate),
-                               ptr(s->param), ptr(s->grad), ptr(s->m1), ptr(s->m2), ptr(s->dacc), ptr(s->img),
+                               ptr(s->param), ptr(s->grad), ptr(s->m1), ptr(s->m2), ptr(s->dacc), ptr(s->img), ptr(s->corr),
                                ptr(s->ia), ptr(s->ib), ptr(s->gbuf[0]), ptr(s->gbuf[1])};
     for (int c = 0; c < 5; ++c) k.push_back(bits(cw.w[c]));
     for (int l = 0; l <= s->nl; ++l) k.push_back(ptr(s->act[l]));
@@ -1339,6 +1341,7 @@ spo_status spo_surrogate_destroy(spo_surrogate *s) {
     cudaFree(s->feat);
     cudaFree(s->img);
     cudaFree(s->tstate);
+    cudaFree(s->corr);
     if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     delete s;
@@ -1489,10 +1492,30 @@ spo_status spo_surrogate_train(spo_surrogate *s, const spo_set *teacher, int64_t
         s->tstate = nullptr;
         return fail(SPO_ENOMEM, "training step state");
     }
+    // Adam's bias corrections of the call's steps, as the host computes them
+    if (s->corr_cap < steps) {
+        cudaFree(s->corr);
+        s->corr = nullptr;
+        s->corr_cap = 0;
+        if (cudaMalloc(&s->corr, sizeof(float2) * (size_t)std::max<int64_t>(steps, 64)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPO_ENOMEM, "training step table");
+        }
+        s->corr_cap = std::max<int64_t>(steps, 64);
+    }
+    std::vector<float2> corr((size_t)steps);
+    for (int64_t j = 0; j < steps; ++j) {
+        const double t = (double)(s->adam_t + j + 1);
+        corr[(size_t)j] = make_float2((float)(1.0 - std::pow((double)s->beta1, t)),
+                                      (float)(1.0 - std::pow((double)s->beta2, t)));
+    }
     ChannelWeights cw{};
     double loss_h = 0.0;
-    train_begin_kernel<<<1, 1, 0, st>>>(s->tstate, lr, s->adam_t);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = steps > 0 ? cudaMemcpyAsync(s->corr, corr.data(), sizeof(float2) * (size_t)steps,
+                                                cudaMemcpyHostToDevice, st)
+                              : cudaSuccess;
+    train_begin_kernel<<<1, 1, 0, st>>>(s->tstate, lr);
+    if (e == cudaSuccess) e = cudaGetLastError();
     for (int64_t step = 0; step < steps && e == cudaSuccess; ++step) {
         const int64_t k = step % run;
         if (k == 0) {   // the next run's samples and their spline values (restarts the sample index)
