@@ -555,7 +555,8 @@ def run_ours(args):
         "config": dict(base_config(cfg, storage, kind, P), algo=algo, brick_vec=args.brick_vec,
                        brick_tile=args.brick_tile, brick_schedule=args.brick_schedule),
         "roofline": roofline, "e2e": e2e,
-        "gpu_launches": args.steps * (1 if algo == "gather" else 3),   # binning: count (+ scan) and scatter
+        # binning (count with its scan, scatter, weight records) and the evaluation
+        "gpu_launches": args.steps * (1 if algo == "gather" else 4),
         "clocks": sampler.summary(),
     }
     if world > 1:
@@ -915,7 +916,7 @@ def measure_crowd(args, kind, steps):
     out.update({"value": evals / (g_ms * 1e-3), "unit": "evals/s",
                 "graph_ms_per_step": round(g_ms, 5), "batch_eval_ms_per_step": round(e_ms, 5),
                 "per_walker_calls_ms_per_step": round(w_ms, 5),
-                "gpu_launches_per_step": "1 graph (item_of, count, scan, scatter, brick kernel "
+                "gpu_launches_per_step": "1 graph (item_of, count, scan, scatter, records, brick kernel "
                                          "+ 1 memset)"})
     for st in sets:
         st.close()

@@ -91,7 +91,7 @@ __global__ void batch_scatter_kernel(const spo_work *__restrict__ items,
                                      const __grid_constant__ BatchParams bp,
                                      const int *__restrict__ keys, const int *__restrict__ slots,
                                      const int *__restrict__ offsets, float4 *__restrict__ sorted,
-                                     float4 *__restrict__ wrec, float **__restrict__ dst) {
+                                     float **__restrict__ dst) {
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < Ptot;
          g += (int64_t)gridDim.x * blockDim.x) {
         const int i = item_of[g];
@@ -99,13 +99,39 @@ __global__ void batch_scatter_kernel(const spo_work *__restrict__ items,
         const spo_work it = items[i];
         const BatchSetDesc &d = bp.sets[it.set];
         const int idx = offsets[keys[g]] + slots[g];
-        const float4 r = make_float4(__ldg(it.pos + 3 * l), __ldg(it.pos + 3 * l + 1),
-                                     __ldg(it.pos + 3 * l + 2), __int_as_float((int)g));
-        sorted[idx] = r;
-        // the position's basis weights, formed once for every orbital tile
-        spo_dev::make_weight_record(r, (int)g, d.gx, d.gy, d.gz,
-                                    wrec + (int64_t)idx * spo_detail::kWeightRecordF4);
+        sorted[idx] = make_float4(__ldg(it.pos + 3 * l), __ldg(it.pos + 3 * l + 1), __ldg(it.pos + 3 * l + 2),
+                                  __int_as_float((int)g));
         dst[idx] = it.out + l * d.rows * d.N;
+    }
+}
+
+constexpr int kRecThreads = 256;
+
+// The weight record of every sorted slot (the position's basis weights,
+// formed once for every orbital tile), one thread per slot: a warp's 32
+// records are formed in shared memory and copied out as contiguous 16-byte
+// stores (formed in the scatter, at scattered slots, the records were
+// written at about a fifth of the DRAM rate).
+__global__ void __launch_bounds__(kRecThreads)
+batch_records_kernel(const spo_work *__restrict__ items, const int *__restrict__ item_of, int64_t Ptot,
+                     const __grid_constant__ BatchParams bp, const float4 *__restrict__ sorted,
+                     float4 *__restrict__ wrec) {
+    constexpr int R = spo_detail::kWeightRecordF4;
+    __shared__ float4 stage[kRecThreads * R];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *ws = stage + warp * 32 * R;
+    for (int64_t base = (int64_t)blockIdx.x * kRecThreads; base < Ptot; base += (int64_t)gridDim.x * kRecThreads) {
+        const int64_t idx = base + threadIdx.x, w0 = base + warp * 32;
+        if (idx < Ptot) {
+            const float4 r = sorted[idx];
+            const int g = __float_as_int(r.w);
+            const BatchSetDesc &d = bp.sets[items[item_of[g]].set];
+            spo_dev::make_weight_record(r, g, d.gx, d.gy, d.gz, ws + lane * R);
+        }
+        __syncwarp();
+        const int64_t n = Ptot - w0 < 32 ? Ptot - w0 : 32;   // records of this warp (none past the end)
+        for (int64_t c = lane; c < n * R; c += 32) wrec[w0 * R + c] = ws[c];
+        __syncwarp();
     }
 }
 
@@ -207,7 +233,13 @@ spo_status queue_work(spo_batch *b, spo_kind kind, int nitems, int64_t Ptot, boo
     if (e == cudaSuccess) {
         batch_scatter_kernel<<<blocks, threads, 0, stream>>>(b->d_items, b->d_start, b->d_item_of, Ptot,
                                                              bp, b->keys, b->slots, b->offsets,
-                                                             b->sorted, b->wrec, b->dst);
+                                                             b->sorted, b->dst);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int rb = (int)std::min<int64_t>((Ptot + kRecThreads - 1) / kRecThreads, 152 * 8);
+        batch_records_kernel<<<rb, kRecThreads, 0, stream>>>(b->d_items, b->d_item_of, Ptot, bp, b->sorted,
+                                                              b->wrec);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess)

@@ -10,11 +10,15 @@
 //                         the ticket) for the next call, so no block waits
 //                         on another and no memset is needed
 //   2. bin_scatter_kernel: perm[offsets[key] + slot] = position index, and
-//                         the position with its index in the same sorted slot;
-//                         when the workspace has room for them, also the
-//                         position's weight record (its 36 basis weights,
-//                         cells and index: the brick kernel's slot), formed
-//                         once here instead of once per orbital tile
+//                         the position with its index in the same sorted slot
+//   3. bin_records_kernel: when the workspace has room for them, the weight
+//                         record of every sorted slot (its position's 36
+//                         basis weights, cells and index: the brick kernel's
+//                         slot), formed once here instead of once per orbital
+//                         tile; one thread per sorted slot, so that a warp's
+//                         32 records (5.6 KB) leave as contiguous stores
+//                         (written from the scatter, at scattered slots,
+//                         they ran at about a fifth of the DRAM rate)
 // (bin_scan_kernel is the stand-alone scan, used by the crowd binning.)
 //
 // The order inside a brick depends on atomic arrival order; every output of
@@ -133,21 +137,45 @@ bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis
 
 __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
                                    const int *__restrict__ slots, const int *__restrict__ offsets,
-                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P,
-                                   GridAxis gx, GridAxis gy, GridAxis gz, float4 *__restrict__ wrec) {
+                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P) {
     grid_dependency_wait();     // the counts, keys, slots and offsets are complete
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = offsets[keys[p]] + slots[p];
         perm[i] = (int)p;
-        const float4 r = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
-                                     __int_as_float((int)p));
-        sorted[i] = r;
-        if (wrec) make_weight_record(r, (int)p, gx, gy, gz, wrec + (int64_t)i * kSlotF4);
+        sorted[i] = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
+                                __int_as_float((int)p));
     }
-    // the brick kernel's CTAs may be scheduled (they issue their table copies
-    // and wait for this grid); the CTA triggers after all its threads'
-    // writes, so the wait covers them where a dependency ends at the trigger
+    // the next grid's CTAs may be scheduled (the brick kernel's issue their
+    // table copies) and wait for this grid; the CTA triggers after all its
+    // threads' writes, so the wait covers them where a dependency ends at
+    // the trigger
+    __syncthreads();
+    grid_dependents_launch();
+}
+
+constexpr int kRecThreads = 256;
+
+// The weight record of every sorted slot, a warp's 32 records formed in
+// shared memory and copied out as contiguous 16-byte stores.
+__global__ void __launch_bounds__(kRecThreads)
+bin_records_kernel(const float4 *__restrict__ sorted, int64_t P, GridAxis gx, GridAxis gy, GridAxis gz,
+                   float4 *__restrict__ wrec) {
+    __shared__ float4 stage[kRecThreads * kSlotF4];
+    grid_dependency_wait();     // the sorted positions are complete
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *ws = stage + warp * 32 * kSlotF4;
+    for (int64_t base = (int64_t)blockIdx.x * kRecThreads; base < P; base += (int64_t)gridDim.x * kRecThreads) {
+        const int64_t i = base + threadIdx.x, w0 = base + warp * 32;
+        if (i < P) {
+            const float4 r = sorted[i];
+            make_weight_record(r, __float_as_int(r.w), gx, gy, gz, ws + lane * kSlotF4);
+        }
+        __syncwarp();
+        const int64_t n = P - w0 < 32 ? P - w0 : 32;   // records of this warp (none past the end)
+        for (int64_t c = lane; c < n * kSlotF4; c += 32) wrec[w0 * kSlotF4 + c] = ws[c];
+        __syncwarp();
+    }
     __syncthreads();
     grid_dependents_launch();
 }
@@ -185,9 +213,15 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     cfg.stream = stream;
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, bin_scatter_kernel, pos, (const int *)w.keys, (const int *)w.slots,
-                              (const int *)w.offsets, w.perm, w.sorted, P, grid_axis(nx), grid_axis(ny),
-                              grid_axis(nz), w.wrec);
+    e = cudaLaunchKernelEx(&cfg, bin_scatter_kernel, pos, (const int *)w.keys, (const int *)w.slots,
+                           (const int *)w.offsets, w.perm, w.sorted, P);
+    if (e != cudaSuccess || !w.wrec) return e;
+    // the records, a programmatic dependent of the scatter as well
+    cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((P + kRecThreads - 1) / kRecThreads,
+                                                                        152 * 8)));
+    cfg.blockDim = dim3((unsigned)kRecThreads);
+    return cudaLaunchKernelEx(&cfg, bin_records_kernel, (const float4 *)w.sorted, P, grid_axis(nx),
+                              grid_axis(ny), grid_axis(nz), w.wrec);
 }
 
 }  // namespace spo_detail
