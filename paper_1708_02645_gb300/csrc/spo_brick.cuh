@@ -82,9 +82,13 @@ constexpr size_t kSlotBytes = (size_t)(BrickShape<TILE>::threads / (TILE / V)) *
 // orbital tile copies them into its slots; without REC the slots are formed
 // here from the sorted position records (the allocation-free entry point,
 // whose fixed scratch holds no records).
+// The pair form runs 3 CTAs per SM with FP32 blocks (72 KB of shared memory
+// each) and 4 with 16-bit blocks (half the bytes; 128 registers, a few
+// bytes spilled): BF16 VGH 0.483 -> 0.467 ms, FP16 0.553 -> 0.539 ms.
 template <typename T, int KIND, int TILE, int V, bool VEC_OUT, bool RATIO = false, bool PAIR = false,
           bool REC = true>
-__global__ void __launch_bounds__(BrickShape<TILE>::threads, PAIR ? 3 : BrickShape<TILE>::ctas_per_sm)
+__global__ void __launch_bounds__(BrickShape<TILE>::threads,
+                                  PAIR ? (sizeof(T) == 2 ? 4 : 3) : BrickShape<TILE>::ctas_per_sm)
 spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis gy, GridAxis gz,
                  int nby, int nbz, int ntiles, int64_t N, const int *__restrict__ offsets,
                  const float4 *__restrict__ sorted, const float4 *__restrict__ wrec,
