@@ -39,6 +39,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <utility>
 
 #include "spo_batch.h"
@@ -150,7 +151,6 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
     }
 
     const int q = threadIdx.x % TPP;
-    const int64_t o0 = (int64_t)tile * TILE + q * kVec;   // first orbital of this thread
     // positions are taken in rounds of PPR; the trip count of the loop is
     // uniform over each warp (groups past the end sit the round out), so the
     // warp can share the weight slots
@@ -198,47 +198,62 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
             }
             ready = true;
         }
-        if (i < end) {
+        // Evaluates the position whose weight slot is sl on KV orbitals from
+        // orbital o of the tile (lane kq of the position's TILE / KV lanes).
+        auto eval = [&](auto kv, const float4 *sl, int kq) {
+            constexpr int KV = decltype(kv)::value;
             Axis Y, Z;
-            const int4 cells = *reinterpret_cast<const int4 *>(slot + 10);
+            const int4 cells = *reinterpret_cast<const int4 *>(sl + 10);
             const int p = cells.w;
-            unpack4(slot[4], Y.w);
-            unpack4(slot[5], Y.d);
-            unpack4(slot[6], Y.dd);
-            unpack4(slot[7], Z.w);
-            unpack4(slot[8], Z.d);
-            unpack4(slot[9], Z.dd);
+            unpack4(sl[4], Y.w);
+            unpack4(sl[5], Y.d);
+            unpack4(sl[6], Y.dd);
+            unpack4(sl[7], Z.w);
+            unpack4(sl[8], Z.d);
+            unpack4(sl[9], Z.dd);
             // the binning put the cell in this brick; the clamp keeps the
             // shared memory index in range even if it had not
             const int lx = min(max(cells.x - bx * kBrick, 0), kBrick - 1);
             const int ly = min(max(cells.y - by * kBrick, 0), kBrick - 1);
             const int lz = min(max(cells.z - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
-            const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + q * kVec;
-            float acc[NC][kVec];
-            window_reduce_staged<KIND, kVec, true>(slot, Y, Z,
+            const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + kq * KV;
+            const int64_t ko0 = (int64_t)tile * TILE + kq * KV;   // first orbital of this lane
+            float acc[NC][KV];
+            window_reduce_staged<KIND, KV, true>(sl, Y, Z,
                                 [&](int a, int b, int g, float *v) {
-                                    load_coefs<T, kVec, false>(
+                                    load_coefs<T, KV, false>(
                                         base + ((a * kBlockEdge + b) * kBZ + g) * TILE, v);
                                 },
                                 acc);
             if constexpr (RATIO) {
                 int r = ra.row_of ? __ldg(ra.row_of + p) : p;
                 r = (int)min(max((int64_t)r, (int64_t)0), ra.nrows - 1);
-                const float *arow = ra.rows + (int64_t)r * ra.ld + o0;
+                const float *arow = ra.rows + (int64_t)r * ra.ld + ko0;
                 float dot = 0.0f;
 #pragma unroll
-                for (int k = 0; k < kVec; ++k)
-                    if (o0 + k < N) dot = fmaf(acc[0][k], __ldg(arow + k), dot);
+                for (int k = 0; k < KV; ++k)
+                    if (ko0 + k < N) dot = fmaf(acc[0][k], __ldg(arow + k), dot);
                 // the TPP lanes of this position form an aligned group of the warp
                 const unsigned lane = threadIdx.x & 31u;
                 const unsigned gmask = TPP >= 32 ? 0xffffffffu
                                                  : (((1u << TPP) - 1u) << (lane & ~(unsigned)(TPP - 1)));
 #pragma unroll
                 for (int off = TPP / 2; off > 0; off >>= 1) dot += __shfl_xor_sync(gmask, dot, off);
-                if (q == 0) ra.partials[(int64_t)tile * ra.P + p] = dot;
+                if (kq == 0) ra.partials[(int64_t)tile * ra.P + p] = dot;
             }
-            if (o0 < N && (!RATIO || out != nullptr))
-                store_rows<NC, kVec, VEC_OUT>(out + (int64_t)p * NC * N + o0, N, N - o0, acc);
+            if (ko0 < N && (!RATIO || out != nullptr))
+                store_rows<NC, KV, VEC_OUT>(out + (int64_t)p * NC * N + ko0, N, N - ko0, acc);
+        };
+        // A warp whose last round holds 1 or 2 positions gives each of them
+        // 16 lanes of 2 orbitals (the same arithmetic per orbital, so the
+        // same bits) instead of running with 2 or 3 of its 4 groups idle.
+        constexpr bool kRemap = !RATIO && kVec == 4 && TPP == 8;
+        if (kRemap && end - ib <= 2) {
+            const int half = (int)(threadIdx.x & 31) >> 4;
+            if (half < end - ib) eval(std::integral_constant<int, 2>{}, wslots + (wg0 + half) * kSlotF4,
+                                      (int)(threadIdx.x & 15));
+        } else if (i < end) {
+            eval(std::integral_constant<int, kVec>{}, slot, q);
         }
 #pragma unroll
         for (int k = 0; k < NPART; ++k) cur[k] = nxt[k];
