@@ -644,7 +644,9 @@ def measure_variants(args, cfg, coefs32, s32, pos, out32, kind, storage, algo, o
             for kd in ("v", "vgl", "vgh"):
                 o = torch.empty(sv.out_shape(n32.P, kd), dtype=torch.float32, device=pos.device)
                 a = resolve_algo(args.algo, sv, n32.P, kd)
-                step_ms = time_steps(sv, p32, o, kd, a, steps, 3)
+                # a step is about 0.06 ms, launched from Python: the median of
+                # three runs of 200 keeps a host stall from entering the number
+                step_ms = float(np.median([time_steps(sv, p32, o, kd, a, 200, 3) for _ in range(3)]))
                 res[f"{n32.name}_{kd}"] = {"value": n32.P * n32.N / (step_ms * 1e-3), "unit": "evals/s",
                                            "ms_per_step": round(step_ms, 5), "algo": a}
     return res
