@@ -145,3 +145,19 @@ def test_workload_config_names_the_bench_shapes():
     assert cfg.grid == (64, 64, 64) and cfg.N == 384 and cfg.P == 98304
     c = bench.base_config(cfg, "f32", "vgh", cfg.P)
     assert c["workload"] == "nio64_64cubed_n384" and c["positions"] == 98304 and c["orbitals"] == 384
+
+
+def test_variant_names_and_surrogate_recipe():
+    """--variants accepts the surrogate-inference timing and refuses unknown
+    names; the specified surrogate is 16 levels x 2^19 x 2, resolutions
+    2..64, 3 x 128 hidden units, with the value channel's loss weight
+    doubled."""
+    import pytest
+    assert "surrogate_inference" in bench.VARIANTS and "all" in bench.VARIANTS
+    with pytest.raises(SystemExit):
+        bench.main(["--variants", "no_such_variant"])
+    spec = bench.surrogate_spec(384)
+    assert (spec.levels, spec.log2_table, spec.features, spec.r_min, spec.r_max, spec.hidden, spec.layers,
+            spec.N) == (16, 19, 2, 2, 64, 128, 3, 384)
+    assert bench.surrogate_spec(384, 16, 512).r_max == 512
+    assert tuple(bench.SURROGATE_CHANNEL_SCALE) == (2.0, 1.0, 1.0, 1.0, 1.0)
