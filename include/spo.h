@@ -444,9 +444,13 @@ spo_status spo_surrogate_destroy(spo_surrogate *s);
 spo_status spo_reserve(spo_set *set, int64_t P, void *stream);
 
 /* Device-side status word of the current device: bit 0 = a bounded wait on a
- * TMA copy gave up (the affected outputs are incomplete).  Synchronises
- * `stream`; with clear != 0 the word is reset to zero afterwards.  Returns
- * SPO_ETIMEOUT if bit 0 was set, SPO_OK otherwise. */
+ * TMA copy gave up (the affected outputs are incomplete); bit 1 = in a
+ * library built with -DSPO_CHECK_BOUNDS (a debug build: the kernels check
+ * the indices they are about to use, such as a position's cell against its
+ * brick, a sorted slot, a permutation entry or a window's table rows), a
+ * check failed and that access was skipped.  Synchronises `stream`; with
+ * clear != 0 the word is reset to zero afterwards.  Returns SPO_ETIMEOUT if
+ * bit 0 was set, SPO_EINVAL if bit 1 was, SPO_OK otherwise. */
 spo_status spo_device_status(unsigned int *flags, int clear, void *stream);
 
 /*

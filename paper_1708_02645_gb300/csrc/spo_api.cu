@@ -561,7 +561,9 @@ spo_status spo_device_status(unsigned int *flags, int clear, void *stream) {
     if (!flags) return fail(SPO_EINVAL, "flags is NULL");
     cudaError_t e = spo_detail::read_device_status(flags, clear != 0, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "device status read");
-    return (*flags & 1u) ? fail(SPO_ETIMEOUT, "a bounded wait on a TMA copy gave up") : SPO_OK;
+    if (*flags & 1u) return fail(SPO_ETIMEOUT, "a bounded wait on a TMA copy gave up");
+    if (*flags & 2u) return fail(SPO_EINVAL, "an index check failed (SPO_CHECK_BOUNDS build); the access was skipped");
+    return SPO_OK;
 }
 
 // Device address of pinned, mapped host memory, or nullptr for any other

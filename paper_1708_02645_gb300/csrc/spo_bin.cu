@@ -104,7 +104,7 @@ bin_scan_kernel(int *__restrict__ counts, int *__restrict__ offsets, int n) {
 __global__ void __launch_bounds__(kCountThreads)
 bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis gy, GridAxis gz, int nby,
                  int nbz, int nbins, int *__restrict__ counts, int *__restrict__ offsets,
-                 int *__restrict__ keys, int *__restrict__ slots) {
+                 int *__restrict__ keys, int *__restrict__ slots, unsigned int *__restrict__ status) {
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         int cx, cy, cz;
@@ -112,7 +112,8 @@ bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis
         reduce_axis(__ldg(pos + 3 * p + 0), gx, cx, t);
         reduce_axis(__ldg(pos + 3 * p + 1), gy, cy, t);
         reduce_axis(__ldg(pos + 3 * p + 2), gz, cz, t);
-        const int key = ((cx / kBrick) * nby + cy / kBrick) * nbz + cz / kBrick;
+        int key = ((cx / kBrick) * nby + cy / kBrick) * nbz + cz / kBrick;
+        if (!bounds_ok(key >= 0 && key < nbins, status)) key = 0;   // debug builds
         keys[p] = key;
         slots[p] = atomicAdd(counts + key, 1);
     }
@@ -137,11 +138,13 @@ bin_count_kernel(const float *__restrict__ pos, int64_t P, GridAxis gx, GridAxis
 
 __global__ void bin_scatter_kernel(const float *__restrict__ pos, const int *__restrict__ keys,
                                    const int *__restrict__ slots, const int *__restrict__ offsets,
-                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P) {
+                                   int *__restrict__ perm, float4 *__restrict__ sorted, int64_t P,
+                                   unsigned int *__restrict__ status) {
     grid_dependency_wait();     // the counts, keys, slots and offsets are complete
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int i = offsets[keys[p]] + slots[p];
+        if (!bounds_ok(i >= 0 && i < P, status)) continue;   // debug builds: a sorted slot in range
         perm[i] = (int)p;
         sorted[i] = make_float4(__ldg(pos + 3 * p), __ldg(pos + 3 * p + 1), __ldg(pos + 3 * p + 2),
                                 __int_as_float((int)p));
@@ -197,8 +200,12 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     const int nbins = nbx * nby * nbz;
     const int threads = kCountThreads;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((P + threads - 1) / threads, 152 * 16));
+    unsigned int *status = nullptr;   // the index checks' flag word (SPO_CHECK_BOUNDS builds)
+#ifdef SPO_CHECK_BOUNDS
+    if (cudaError_t es = device_status_address(&status); es != cudaSuccess) return es;
+#endif
     bin_count_kernel<<<blocks, threads, 0, stream>>>(pos, P, grid_axis(nx), grid_axis(ny), grid_axis(nz), nby,
-                                                     nbz, nbins, w.counts, w.offsets, w.keys, w.slots);
+                                                     nbz, nbins, w.counts, w.offsets, w.keys, w.slots, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // programmatic dependent launch: the scatter is scheduled while the
@@ -214,7 +221,7 @@ cudaError_t launch_bin(const float *pos, int64_t P, int nx, int ny, int nz, int 
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, bin_scatter_kernel, pos, (const int *)w.keys, (const int *)w.slots,
-                           (const int *)w.offsets, w.perm, w.sorted, P);
+                           (const int *)w.offsets, w.perm, w.sorted, P, status);
     if (e != cudaSuccess || !w.wrec) return e;
     // the records, a programmatic dependent of the scatter as well
     cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>((P + kRecThreads - 1) / kRecThreads,

@@ -212,10 +212,16 @@ spo_brick_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, GridAxis 
             unpack4(sl[8], Z.d);
             unpack4(sl[9], Z.dd);
             // the binning put the cell in this brick; the clamp keeps the
-            // shared memory index in range even if it had not
-            const int lx = min(max(cells.x - bx * kBrick, 0), kBrick - 1);
-            const int ly = min(max(cells.y - by * kBrick, 0), kBrick - 1);
-            const int lz = min(max(cells.z - bz * kBrick, 0), (PAIR ? 2 : 1) * kBrick - 1);
+            // shared memory index in range even if it had not (debug builds
+            // check it, and the record's position index)
+            const int ux = cells.x - bx * kBrick, uy = cells.y - by * kBrick, uz = cells.z - bz * kBrick;
+            if (!bounds_ok(ux >= 0 && ux < kBrick && uy >= 0 && uy < kBrick && uz >= 0 &&
+                               uz < (PAIR ? 2 : 1) * kBrick && p >= 0,
+                           status))
+                return;
+            const int lx = min(max(ux, 0), kBrick - 1);
+            const int ly = min(max(uy, 0), kBrick - 1);
+            const int lz = min(max(uz, 0), (PAIR ? 2 : 1) * kBrick - 1);
             const T *base = block + ((lx * kBlockEdge + ly) * kBZ + lz) * TILE + kq * KV;
             const int64_t ko0 = (int64_t)tile * TILE + kq * KV;   // first orbital of this lane
             float acc[NC][KV];
@@ -438,13 +444,17 @@ spo_brick_pipe_kernel(const __grid_constant__ CUtensorMap map, GridAxis gx, Grid
             make_xaxis(rec.x, gx, X);
             make_axis(rec.y, gy, Y);
             make_axis(rec.z, gz, Z);
-            const int lx = min(max(X.cell - sm.bx * kBrick, 0), kBrick - 1);
-            const int ly = min(max(Y.cell - sm.by * kBrick, 0), kBrick - 1);
-            const int lz = min(max(Z.cell - sm.bz * kBrick, 0), kBrick - 1);
+            const int ux = X.cell - sm.bx * kBrick, uy = Y.cell - sm.by * kBrick, uz = Z.cell - sm.bz * kBrick;
+            const bool inside = bounds_ok(ux >= 0 && ux < kBrick && uy >= 0 && uy < kBrick && uz >= 0 &&
+                                              uz < kBrick && p >= 0,
+                                          status);
+            const int lx = min(max(ux, 0), kBrick - 1);
+            const int ly = min(max(uy, 0), kBrick - 1);
+            const int lz = min(max(uz, 0), kBrick - 1);
             const T *block = reinterpret_cast<const T *>(smem + (size_t)slot * Shape::block_stride);
             const int64_t tile0 = (int64_t)sm.tile * TILE;
 #pragma unroll 1
-            for (int pass = 0; pass < PASSES; ++pass) {
+            for (int pass = 0; pass < PASSES && inside; ++pass) {
                 const int o_tile = pass * 32 + gl * kVec;   // orbital within the tile
                 const T *base = block + ((lx * kBlockEdge + ly) * kBlockEdge + lz) * TILE + o_tile;
                 float acc[NC][kVec];

@@ -19,6 +19,23 @@ struct Rows {
 };
 
 // ---------------------------------------------------------------------------
+// debug builds (-DSPO_CHECK_BOUNDS): index checks inside the kernels
+// ---------------------------------------------------------------------------
+// An index the kernel is about to use satisfies `cond`; when it does not,
+// bit 1 of the device status word is set and the caller skips the access.
+// Without SPO_CHECK_BOUNDS this is `true` and costs nothing.
+__device__ __forceinline__ bool bounds_ok(bool cond, unsigned int *status) {
+#ifdef SPO_CHECK_BOUNDS
+    if (!cond && status) atomicOr(status, 2u);
+    return cond;
+#else
+    (void)cond;
+    (void)status;
+    return true;
+#endif
+}
+
+// ---------------------------------------------------------------------------
 // widening loads of V = 2 or 4 consecutive coefficients (global memory via
 // the read-only path, or shared memory)
 // ---------------------------------------------------------------------------

@@ -11,6 +11,7 @@
 // threads read neighbouring windows and L2 serves most of the corner rows.
 #include <algorithm>
 
+#include "spo_batch.h"
 #include "spo_device.cuh"
 #include "spo_index.cuh"
 #include "spo_internal.h"
@@ -29,7 +30,7 @@ template <typename T, int KIND, bool VEC_OUT>
 __global__ void __launch_bounds__(kThreads, 2)
 spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxis gz, int yp, int zp,
                   int64_t Np, int64_t N, const float *__restrict__ pos, const int *__restrict__ perm,
-                  int64_t P, int G, float *__restrict__ out)
+                  int64_t P, int G, float *__restrict__ out, unsigned int *__restrict__ status)
 {
     constexpr int NC = Rows<KIND>::value;
     const int64_t item = (int64_t)blockIdx.x * kThreads + threadIdx.x;
@@ -37,12 +38,18 @@ spo_gather_kernel(const T *__restrict__ table, GridAxis gx, GridAxis gy, GridAxi
     int q;
     const int64_t i = div_index(item, G, q);
     const int64_t p = perm ? (int64_t)__ldg(perm + i) : i;
+    if (!bounds_ok(p >= 0 && p < P, status)) return;   // debug builds: a permutation entry in range
 
     XAxis X;
     Axis Y, Z;
     make_xaxis(__ldg(pos + 3 * p + 0), gx, X);
     make_axis(__ldg(pos + 3 * p + 1), gy, Y);
     make_axis(__ldg(pos + 3 * p + 2), gz, Z);
+    // debug builds: the window's 4 x 4 x 4 padded nodes lie in the table
+    if (!bounds_ok((unsigned)X.cell < (unsigned)gx.n && (unsigned)Y.cell < (unsigned)gy.n &&
+                       (unsigned)Z.cell < (unsigned)gz.n,
+                   status))
+        return;
 
     // padded node of corner (a, b, g) = (cell_x + a, cell_y + b, cell_z + g)
     const T *tq = table + (((int64_t)X.cell * yp + Y.cell) * zp + Z.cell) * Np + (int64_t)q * kVec;
@@ -65,14 +72,18 @@ cudaError_t gather_typed(const spo_detail::TableView &t, const float *pos, const
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const bool vec_out = (t.N % kVec == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
     const T *table = static_cast<const T *>(t.table);
+    unsigned int *status = nullptr;   // the index checks' flag word (SPO_CHECK_BOUNDS builds)
+#ifdef SPO_CHECK_BOUNDS
+    if (cudaError_t e = spo_detail::device_status_address(&status); e != cudaSuccess) return e;
+#endif
     if (vec_out)
         spo_gather_kernel<T, KIND, true><<<(unsigned)blocks, kThreads, 0, stream>>>(
             table, grid_axis(t.nx), grid_axis(t.ny), grid_axis(t.nz), t.yp, t.zp, t.Np, t.N, pos,
-            perm, P, G, out);
+            perm, P, G, out, status);
     else
         spo_gather_kernel<T, KIND, false><<<(unsigned)blocks, kThreads, 0, stream>>>(
             table, grid_axis(t.nx), grid_axis(t.ny), grid_axis(t.nz), t.yp, t.zp, t.Np, t.N, pos,
-            perm, P, G, out);
+            perm, P, G, out, status);
     return cudaGetLastError();
 }
 

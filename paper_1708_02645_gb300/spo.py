@@ -100,7 +100,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The in-tree libspo.so, or the library named by SPO_LIBRARY (another
+    build of it, such as the index-checking debug build)."""
+    return os.environ.get("SPO_LIBRARY") or _build.LIB
 
 
 def load() -> ctypes.CDLL:
@@ -157,7 +159,9 @@ def _dtype_of(coefs, src_dtype):
 
 def device_status(clear: bool = True, stream=None) -> int:
     """Device-side status word of the current device (bit 0: a bounded wait
-    on a TMA copy gave up).  Raises SpoError(SPO_ETIMEOUT) if bit 0 is set."""
+    on a TMA copy gave up; bit 1: an index check of a -DSPO_CHECK_BOUNDS build
+    failed).  Raises SpoError(SPO_ETIMEOUT) if bit 0 is set, SpoError(SPO_EINVAL)
+    if bit 1 is."""
     flags = ctypes.c_uint()
     _check(load().spo_device_status(ctypes.byref(flags), int(clear), _stream_handle(stream)),
            "spo_device_status")

@@ -125,3 +125,18 @@ def test_newer_entry_points_reject_bad_arguments_before_cuda(lib):
     assert lib.spo_selftest_wait(1000, None, None) == 1
     assert lib.spo_eval_batch(None, 0, None, 0, 2, None) == 1
     assert lib.spo_batch_create(None, 0, 1, 1, ctypes.byref(h)) == 1
+
+
+def test_bounds_checked_units_compile():
+    """The index-checking debug flavour (-DSPO_CHECK_BOUNDS) of the gather
+    and binning units compiles (cross-compiled here; the GPU test builds and
+    runs the whole checked library)."""
+    import subprocess
+    import tempfile
+    from paper_1708_02645_gb300 import build
+    with tempfile.TemporaryDirectory() as d:
+        for src in ("spo_eval.cu", "spo_bin.cu"):
+            cmd = [build.nvcc(), *build.ARCH, *build.NVCC_FLAGS, "-DSPO_CHECK_BOUNDS", "-c",
+                   os.path.join(build.CSRC, src), "-o", os.path.join(d, src + ".o")]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr[-2000:]
